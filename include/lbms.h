@@ -1,0 +1,177 @@
+/*
+ * lbms.h -- C ABI of a GB300 (sm_103a) lattice Boltzmann solver for
+ * multicomponent diffusion after the Maxwell-Stefan multiple-relaxation-time
+ * model of Chai, Guo, Wang and Shi (arXiv:1808.06787).
+ *
+ * The model (Sec. 3.1): n species, of which the first S = n - 1 carry
+ * distribution functions f_k^i on a DdQq lattice; the last species follows from
+ * the closure sum_i xi_i = 1 (Eq. 2-3b).  One time step is the collision of
+ * Eq. 3-13a with the cross-species relaxation matrices Lambda^{ij} followed by
+ * the propagation of Eq. 3-13b.  At every node the library evaluates
+ *   xi_i = sum_k f_k^i                                       (Eq. 3-15)
+ *   B(xi, D_ij)                                              (Eq. 2-10)
+ *   Lambda_1 with D~ = B^{-1} = c_s^2 (Lambda_1^{-1} - I/2)   (Eqs. 2-11, 3-26)
+ *   Lambda_2 from Lambda_1                                   (Eq. 3-16)
+ *   f_eq = w_k xi_i                                          (Eq. 3-3)
+ * in lattice units (dx = dt = c = 1, c_t = 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Fields are species-major and x-fastest: a mole-fraction field is
+ *   x[sigma][z][y][x] with sigma = 0..n-1; a flux field is
+ *   J[sigma][a][z][y][x] with a = 0..dim-1.  2D lattices use nz = 1.
+ * - Element type of every field is the handle's dtype (float or double).
+ * - Buffers may be device memory or host memory; the library asks the CUDA
+ *   runtime which one a pointer is.  Host buffers are copied through a bounded
+ *   staging area of the workspace; pinned host memory gives full bandwidth.
+ * - Everything is ordered on the handle's CUDA stream.  Calls that return data
+ *   to host memory (lbms_mass, host outputs of lbms_moments) synchronise that
+ *   stream; all other calls are asynchronous.
+ * - The library allocates no device memory.  The caller owns the workspace and
+ *   every field buffer.  The handle itself is a small host allocation.
+ * - Errors are reported by return code; lbms_last_error() gives a message.
+ *   Nothing aborts, exits or traps on the device.  Kernels raise status flags
+ *   that lbms_status() reads.
+ * - Not thread-safe per handle: one host thread drives a handle at a time.
+ */
+#ifndef LBMS_H
+#define LBMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbms_s lbms_t;
+
+/* Lattices of Sec. 3.1: D2Q5 (Eq. 3-7), D2Q9 (Eq. 3-8), D3Q7 (Eq. 3-10). */
+enum { LBMS_D2Q5 = 0, LBMS_D2Q9 = 1, LBMS_D3Q7 = 2 };
+
+/* Storage and arithmetic type of the populations and of all fields. */
+enum { LBMS_F32 = 0, LBMS_F64 = 1 };
+
+/* Face kinds.  PERIODIC wraps (used in all experiments of Sec. 4); NOFLUX is the
+ * half-way bounce-back of Sec. 4, f_k(x_f, t+1) = f+_kbar(x_f, t). */
+enum { LBMS_PERIODIC = 0, LBMS_NOFLUX = 1 };
+
+/* Relaxation of the even moments.  MAGIC: Lambda_2 by Eq. 3-16 (off-diagonal
+ * entries equal Lambda_1, diagonal 8 (l - 2) / (l - 8)).  SRT: Lambda_2 =
+ * Lambda_1, the single-relaxation-time reduction of Sec. 3.1 used for the
+ * comparison of Sec. 4.1. */
+enum { LBMS_RELAX_MAGIC = 0, LBMS_RELAX_SRT = 1 };
+
+/* Return codes. */
+enum {
+    LBMS_OK = 0,
+    LBMS_EINVAL = 1,    /* bad argument, size or combination */
+    LBMS_ENOMEM = 2,    /* workspace too small */
+    LBMS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    LBMS_ENONFINITE = 4,
+    LBMS_ERANGE = 5,
+    LBMS_ETIMEOUT = 6
+};
+
+/* Status flags raised by kernels (lbms_status). */
+#define LBMS_FLAG_NONFINITE 0x1u /* a mole fraction became NaN or infinite */
+#define LBMS_FLAG_RANGE 0x2u     /* a mole fraction left [-0.05, 1.05] */
+#define LBMS_FLAG_INIT 0x4u      /* lbms_set_state input not finite or not summing to 1 */
+
+/* Largest number of species and largest grid. */
+#define LBMS_MAX_SPECIES 8
+#define LBMS_MAX_CELLS 2147483647L
+
+/*
+ * Bytes of device workspace that lbms_create needs for this problem: two
+ * population buffers of S * Q * cells elements (ping-pong), per-block FP64
+ * partial sums for the mass diagnostic, a status word and a staging area for
+ * host input/output.  Returns 0 for an invalid combination.
+ */
+size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dtype);
+
+/*
+ * Create a solver handle.
+ *   out        receives the handle (set to NULL on failure).
+ *   lattice    LBMS_D2Q5 | LBMS_D2Q9 | LBMS_D3Q7 (Sec. 3.1).
+ *   n_species  n, 2..8.  S = n - 1 species are evolved (Eq. 3-2, i <= n-1).
+ *   grid       {nx, ny, nz}, each >= 1; nz must be 1 for 2D lattices;
+ *              nx * ny * nz <= LBMS_MAX_CELLS.
+ *   D          host array of n * n binary Maxwell-Stefan diffusivities D_ij in
+ *              lattice units (Eq. 2-7), row-major.  Off-diagonal entries must be
+ *              finite, > 0 and symmetric (D_ij = D_ji); the diagonal is ignored.
+ *   relax      LBMS_RELAX_MAGIC | LBMS_RELAX_SRT.
+ *   bc         host array of 6 face kinds {x-low, x-high, y-low, y-high, z-low,
+ *              z-high}; a periodic face must be paired with a periodic face on
+ *              the same axis.  Unused z faces of a 2D lattice are ignored.
+ *   dtype      LBMS_F32 | LBMS_F64.
+ *   workspace  device memory of at least lbms_workspace_size() bytes, aligned
+ *              to 256 bytes, owned by the caller and kept alive until
+ *              lbms_destroy.
+ *   cuda_stream  cudaStream_t on which all work is ordered (NULL = legacy
+ *              default stream).
+ * The state is undefined until lbms_set_state.  Returns LBMS_EINVAL or
+ * LBMS_ENOMEM for bad arguments, LBMS_ECUDA if the runtime fails.
+ */
+int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], const double* D,
+                int relax, const int bc[6], int dtype, void* workspace, size_t workspace_bytes,
+                void* cuda_stream);
+
+/*
+ * Initialise from mole fractions: f_k^i = w_k xi_i(t = 0) (Sec. 4,
+ * initialisation), i.e. the post-collision state at t = 0.  x0 holds all n
+ * species, [n][nz][ny][nx] of the handle's dtype, host or device.  Each node
+ * must be finite and sum to 1 within 1e-5; otherwise LBMS_FLAG_INIT is raised
+ * (read it with lbms_status) and the state is still written.  Resets the step
+ * counter to 0.
+ */
+int lbms_set_state(lbms_t* h, const void* x0);
+
+/*
+ * Advance n_steps >= 0 time steps of Eqs. 3-13a/3-13b (pull form: each node
+ * gathers f+_k(x - c_k), collides, and stores its post-collision populations).
+ * The last step of each call also writes per-block FP64 partial sums of every
+ * species' mole fraction and reduces them, so lbms_mass after lbms_step reads
+ * no populations.  Asynchronous: launch errors are returned at once, numerical
+ * trouble is raised in the status flags.
+ */
+int lbms_step(lbms_t* h, long n_steps);
+
+/*
+ * Mole fractions and diffusion fluxes at the current time t (Sec. 3.2):
+ *   x_sigma  [n][nz][ny][nx]: xi_i = sum_k f_k^i for i < n-1, and
+ *            xi_n = 1 - sum_i xi_i (Eq. 2-3b).  Required.
+ *   J_sigma  [n][dim][nz][ny][nx] or NULL: J_i = -sum_j D~_ij grad xi_j with the
+ *            local gradient of Eq. xix, evaluated as J = (I - Lambda_1/2) m_1 of
+ *            the pre-collision populations at time t (identical by Eq. 3-26),
+ *            and J_n = -sum_i J_i (Eq. 2-3a).  J is zero at t = 0.
+ * Host or device buffers; host outputs synchronise the stream.
+ */
+int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma);
+
+/*
+ * Total amount of each species, mass_out[i] = sum over nodes of xi_i, for all n
+ * species, in FP64 with compensated (two-sum) accumulation in a fixed order, so
+ * that repeated calls on the same state agree bit for bit.  mass_out is a host
+ * array of n doubles.  Synchronises the stream.
+ */
+int lbms_mass(lbms_t* h, double* mass_out);
+
+/* OR of the status flags raised since lbms_set_state.  Synchronises the stream. */
+int lbms_status(lbms_t* h, uint32_t* flags);
+
+/* Number of steps taken since lbms_set_state, or -1 for a NULL handle. */
+long lbms_steps_done(const lbms_t* h);
+
+/* Message of the last failed call on this handle ("" if none).  With h == NULL,
+ * the message of the last failed lbms_create on this thread. */
+const char* lbms_last_error(const lbms_t* h);
+
+/* Release the handle.  Does not free the caller's workspace. */
+void lbms_destroy(lbms_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMS_H */

@@ -1,0 +1,481 @@
+// Host runtime behind the C ABI of include/lbms.h: argument checks, workspace
+// layout, ping-pong buffers, CUDA-graph replay of step runs, host staging and
+// the deterministic FP64 mass reduction.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbms_internal.h"
+#include "node.cuh"
+
+using namespace lbms;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStagingMax = size_t(16) << 20;  // host I/O chunk area
+constexpr int kGraphSteps = 32;                   // steps per captured graph (even)
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int lattice_q(int lat) { return lat == LBMS_D2Q5 ? 5 : lat == LBMS_D2Q9 ? 9 : lat == LBMS_D3Q7 ? 7 : 0; }
+int lattice_dim(int lat) { return lat == LBMS_D3Q7 ? 3 : 2; }
+
+struct Layout {
+    size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_staging, staging_bytes,
+        total;
+};
+
+bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
+{
+    const int Q = lattice_q(lat);
+    if (!Q || n < 2 || n > LBMS_MAX_SPECIES || !grid) return false;
+    if (dtype != LBMS_F32 && dtype != LBMS_F64) return false;
+    if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) return false;
+    if (lattice_dim(lat) == 2 && grid[2] != 1) return false;
+    const double cells_d = (double)grid[0] * grid[1] * grid[2];
+    if (cells_d > (double)LBMS_MAX_CELLS) return false;
+    const size_t cells = (size_t)grid[0] * grid[1] * grid[2];
+    const size_t es = dtype == LBMS_F64 ? 8 : 4;
+    const int dim = lattice_dim(lat);
+    L->f_bytes = align_up((size_t)(n - 1) * Q * cells * es);
+    L->off_f0 = 0;
+    L->off_f1 = L->f_bytes;
+    L->off_partials = 2 * L->f_bytes;
+    const size_t blocks = node_blocks((uint32_t)cells);
+    L->off_mass = L->off_partials + align_up(blocks * n * sizeof(double2));
+    L->off_status = L->off_mass + align_up(LBMS_MAX_SPECIES * sizeof(double));
+    L->off_staging = L->off_status + kAlign;
+    size_t want = (size_t)n * (1 + dim) * cells * es;
+    L->staging_bytes = align_up(want < kStagingMax ? want : kStagingMax);
+    L->total = L->off_staging + L->staging_bytes;
+    return true;
+}
+
+thread_local char g_create_error[256] = "";
+
+__global__ void k_mass_finalize(const double2* __restrict__ partials, uint32_t blocks, int n,
+                                double* __restrict__ out)
+{
+    __shared__ double2 red[kBlock / 32];
+    const int s = blockIdx.x;
+    double sum = 0.0, comp = 0.0;
+    for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x) {
+        const double2 v = partials[(size_t)b * n + s];
+        two_sum_merge(sum, comp, v.x, v.y);
+    }
+    // same fixed-order block reduction as the step kernel
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double s2 = __shfl_down_sync(0xffffffffu, sum, off);
+        const double c2 = __shfl_down_sync(0xffffffffu, comp, off);
+        two_sum_merge(sum, comp, s2, c2);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = make_double2(sum, comp);
+    __syncthreads();
+    if (warp == 0) {
+        sum = lane < (int)(blockDim.x >> 5) ? red[lane].x : 0.0;
+        comp = lane < (int)(blockDim.x >> 5) ? red[lane].y : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double s2 = __shfl_down_sync(0xffffffffu, sum, off);
+            const double c2 = __shfl_down_sync(0xffffffffu, comp, off);
+            two_sum_merge(sum, comp, s2, c2);
+        }
+        if (lane == 0) out[s] = sum + comp;
+    }
+}
+
+}  // namespace
+
+struct lbms_s {
+    int lattice = 0, n = 0, S = 0, Q = 0, dim = 0, dtype = 0, relax = 0;
+    int nx = 1, ny = 1, nz = 1;
+    uint32_t cells = 0, blocks = 0;
+    uint32_t noflux = 0;
+    size_t es = 4;
+    double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};
+    char* ws = nullptr;
+    Layout lay{};
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;  // f[cur] holds the post-collision populations at time t
+    double2* partials = nullptr;
+    double* mass_dev = nullptr;
+    bool mass_valid = false;
+    uint32_t* status = nullptr;
+    char* staging = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graphs_ok = true;
+    long steps = 0;
+    char err[512] = "";
+};
+
+namespace {
+
+int fail(lbms_t* h, int code, const char* fmt, ...)
+{
+    char* buf = h ? h->err : g_create_error;
+    size_t cap = h ? sizeof(h->err) : sizeof(g_create_error);
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, cap, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(lbms_t* h, cudaError_t e, const char* what)
+{
+    return fail(h, LBMS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaError_t dispatch(const lbms_t* h, Op op, const KArgs& a)
+{
+    switch (h->lattice) {
+        case LBMS_D2Q5: return dispatch_d2q5(op, h->dtype, a);
+        case LBMS_D2Q9: return dispatch_d2q9(op, h->dtype, a);
+        default: return dispatch_d3q7(op, h->dtype, a);
+    }
+}
+
+KArgs base_args(const lbms_t* h, cudaStream_t st)
+{
+    KArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    a.cells = h->cells;
+    a.noflux = h->noflux;
+    a.relax = h->relax;
+    a.n_species = h->n;
+    memcpy(a.invD, h->invD, sizeof(a.invD));
+    a.status = h->status;
+    a.stream = st;
+    return a;
+}
+
+// One step from f[src] into f[1 - src], optionally with mass partials.
+cudaError_t launch_step(const lbms_t* h, int src, bool mass, cudaStream_t st)
+{
+    KArgs a = base_args(h, st);
+    a.fin = h->f[src];
+    a.fout = h->f[1 - src];
+    a.partials = h->partials;
+    return dispatch(h, mass ? OP_STEP_MASS : OP_STEP, a);
+}
+
+cudaError_t launch_finalize(const lbms_t* h, cudaStream_t st)
+{
+    k_mass_finalize<<<h->n, kBlock, 0, st>>>(h->partials, h->blocks, h->n, h->mass_dev);
+    return cudaGetLastError();
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Capture kGraphSteps plain steps starting from buffer `parity`.
+cudaError_t build_graph(lbms_t* h, int parity)
+{
+    cudaError_t e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    int src = parity;
+    for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) {
+        le = launch_step(h, src, false, h->capture);
+        src = 1 - src;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->capture, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dtype)
+{
+    Layout L;
+    return make_layout(lattice, n_species, grid, dtype, &L) ? L.total : 0;
+}
+
+int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], const double* D,
+                int relax, const int bc[6], int dtype, void* workspace, size_t workspace_bytes,
+                void* cuda_stream)
+{
+    g_create_error[0] = '\0';
+    if (!out) return fail(nullptr, LBMS_EINVAL, "out is NULL");
+    *out = nullptr;
+    Layout L;
+    if (!make_layout(lattice, n_species, grid, dtype, &L))
+        return fail(nullptr, LBMS_EINVAL, "invalid lattice/species/grid/dtype combination");
+    if (relax != LBMS_RELAX_MAGIC && relax != LBMS_RELAX_SRT)
+        return fail(nullptr, LBMS_EINVAL, "invalid relaxation mode %d", relax);
+    if (!D || !bc) return fail(nullptr, LBMS_EINVAL, "D and bc must not be NULL");
+    if (!workspace) return fail(nullptr, LBMS_EINVAL, "workspace is NULL");
+    if ((uintptr_t)workspace % kAlign)
+        return fail(nullptr, LBMS_EINVAL, "workspace must be 256-byte aligned");
+    if (workspace_bytes < L.total)
+        return fail(nullptr, LBMS_ENOMEM, "workspace holds %zu bytes, %zu needed", workspace_bytes,
+                    L.total);
+    const int n = n_species;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (i == j) continue;
+            const double d = D[i * n + j];
+            if (!(isfinite(d) && d > 0.0))
+                return fail(nullptr, LBMS_EINVAL, "D[%d][%d] = %g is not finite and positive", i, j, d);
+            if (d != D[j * n + i])
+                return fail(nullptr, LBMS_EINVAL, "D is not symmetric at (%d, %d)", i, j);
+        }
+    const int dim = lattice_dim(lattice);
+    uint32_t noflux = 0;
+    for (int a = 0; a < dim; ++a) {
+        const int lo = bc[2 * a], hi = bc[2 * a + 1];
+        if ((lo != LBMS_PERIODIC && lo != LBMS_NOFLUX) || (hi != LBMS_PERIODIC && hi != LBMS_NOFLUX))
+            return fail(nullptr, LBMS_EINVAL, "invalid face kind on axis %d", a);
+        if ((lo == LBMS_PERIODIC) != (hi == LBMS_PERIODIC))
+            return fail(nullptr, LBMS_EINVAL, "a periodic face must be paired on axis %d", a);
+        if (lo == LBMS_NOFLUX) noflux |= 1u << (2 * a);
+        if (hi == LBMS_NOFLUX) noflux |= 1u << (2 * a + 1);
+    }
+    lbms_t* h = new (std::nothrow) lbms_t;
+    if (!h) return fail(nullptr, LBMS_ENOMEM, "host allocation failed");
+    h->lattice = lattice;
+    h->n = n;
+    h->S = n - 1;
+    h->Q = lattice_q(lattice);
+    h->dim = dim;
+    h->dtype = dtype;
+    h->relax = relax;
+    h->nx = grid[0]; h->ny = grid[1]; h->nz = grid[2];
+    h->cells = (uint32_t)((size_t)grid[0] * grid[1] * grid[2]);
+    h->blocks = node_blocks(h->cells);
+    h->noflux = noflux;
+    h->es = dtype == LBMS_F64 ? 8 : 4;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) h->invD[i][j] = i == j ? 0.0 : 1.0 / D[i * n + j];
+    h->ws = static_cast<char*>(workspace);
+    h->lay = L;
+    h->f[0] = h->ws + L.off_f0;
+    h->f[1] = h->ws + L.off_f1;
+    h->partials = reinterpret_cast<double2*>(h->ws + L.off_partials);
+    h->mass_dev = reinterpret_cast<double*>(h->ws + L.off_mass);
+    h->status = reinterpret_cast<uint32_t*>(h->ws + L.off_status);
+    h->staging = h->ws + L.off_staging;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, LBMS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), h->stream);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(h->capture);
+        delete h;
+        return fail(nullptr, LBMS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return LBMS_OK;
+}
+
+int lbms_set_state(lbms_t* h, const void* x0)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!x0) return fail(h, LBMS_EINVAL, "x0 is NULL");
+    h->err[0] = '\0';
+    cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+    h->cur = 0;
+    h->steps = 0;
+    h->mass_valid = false;
+    KArgs a = base_args(h, h->stream);
+    a.fout = h->f[0];
+    if (is_device_ptr(x0)) {
+        a.field_in = x0;
+        a.c0 = 0; a.c1 = h->cells; a.stride = h->cells;
+        e = dispatch(h, OP_INIT, a);
+        return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "init kernel");
+    }
+    const uint32_t chunk = (uint32_t)(h->lay.staging_bytes / (h->n * h->es));
+    const char* src = static_cast<const char*>(x0);
+    for (uint32_t c0 = 0; c0 < h->cells; c0 += chunk) {
+        const uint32_t c1 = c0 + chunk < h->cells ? c0 + chunk : h->cells;
+        for (int s = 0; s < h->n; ++s) {
+            e = cudaMemcpyAsync(h->staging + (size_t)s * chunk * h->es,
+                                src + ((size_t)s * h->cells + c0) * h->es, (size_t)(c1 - c0) * h->es,
+                                cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (host to device)");
+        }
+        a.field_in = h->staging;
+        a.c0 = c0; a.c1 = c1; a.stride = chunk;
+        e = dispatch(h, OP_INIT, a);
+        if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+    }
+    return LBMS_OK;
+}
+
+int lbms_step(lbms_t* h, long n_steps)
+{
+    if (!h) return LBMS_EINVAL;
+    if (n_steps < 0) return fail(h, LBMS_EINVAL, "n_steps = %ld is negative", n_steps);
+    h->err[0] = '\0';
+    if (n_steps == 0) return LBMS_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
+    const bool use_graphs = h->graphs_ok && cs == cudaStreamCaptureStatusNone;
+    long left = n_steps;
+    while (left > 1) {
+        if (use_graphs && left - 1 >= kGraphSteps) {
+            if (!h->graph[h->cur]) {
+                e = build_graph(h, h->cur);
+                if (e != cudaSuccess) {
+                    // fall back to direct launches for this handle
+                    cudaGetLastError();
+                    h->graphs_ok = false;
+                    break;
+                }
+            }
+            e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            left -= kGraphSteps;
+            h->steps += kGraphSteps;
+            continue;
+        }
+        e = launch_step(h, h->cur, false, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur = 1 - h->cur;
+        --left;
+        ++h->steps;
+    }
+    while (left > 1) {
+        e = launch_step(h, h->cur, false, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur = 1 - h->cur;
+        --left;
+        ++h->steps;
+    }
+    e = launch_step(h, h->cur, true, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+    h->cur = 1 - h->cur;
+    ++h->steps;
+    e = launch_finalize(h, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mass finalize kernel");
+    h->mass_valid = true;
+    return LBMS_OK;
+}
+
+int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!x_sigma) return fail(h, LBMS_EINVAL, "x_sigma is NULL");
+    h->err[0] = '\0';
+    KArgs a = base_args(h, h->stream);
+    a.fin = h->steps > 0 ? h->f[1 - h->cur] : nullptr;
+    a.fout = h->f[h->cur];
+    const bool xdev = is_device_ptr(x_sigma);
+    const bool jdev = J_sigma ? is_device_ptr(J_sigma) : true;
+    cudaError_t e;
+    if (xdev && jdev) {
+        a.field_x = x_sigma;
+        a.field_J = J_sigma;
+        a.c0 = 0; a.c1 = h->cells; a.stride = h->cells;
+        e = dispatch(h, OP_MOMENTS, a);
+        return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "moments kernel");
+    }
+    const int ncomp = h->n * (J_sigma ? 1 + h->dim : 1);
+    const uint32_t chunk = (uint32_t)(h->lay.staging_bytes / (ncomp * h->es));
+    char* xo = static_cast<char*>(x_sigma);
+    char* jo = static_cast<char*>(J_sigma);
+    for (uint32_t c0 = 0; c0 < h->cells; c0 += chunk) {
+        const uint32_t c1 = c0 + chunk < h->cells ? c0 + chunk : h->cells;
+        a.field_x = h->staging;
+        a.field_J = J_sigma ? h->staging + (size_t)h->n * chunk * h->es : nullptr;
+        a.c0 = c0; a.c1 = c1; a.stride = chunk;
+        e = dispatch(h, OP_MOMENTS, a);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+        const size_t len = (size_t)(c1 - c0) * h->es;
+        for (int s = 0; s < h->n; ++s) {
+            e = cudaMemcpyAsync(xo + ((size_t)s * h->cells + c0) * h->es,
+                                h->staging + (size_t)s * chunk * h->es, len, cudaMemcpyDefault,
+                                h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (moments)");
+        }
+        for (int q = 0; J_sigma && q < h->n * h->dim; ++q) {
+            e = cudaMemcpyAsync(jo + ((size_t)q * h->cells + c0) * h->es,
+                                h->staging + ((size_t)h->n + q) * chunk * h->es, len,
+                                cudaMemcpyDefault, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (fluxes)");
+        }
+    }
+    e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaStreamSynchronize");
+}
+
+int lbms_mass(lbms_t* h, double* mass_out)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!mass_out) return fail(h, LBMS_EINVAL, "mass_out is NULL");
+    h->err[0] = '\0';
+    cudaError_t e;
+    if (!h->mass_valid) {
+        KArgs a = base_args(h, h->stream);
+        a.fout = h->f[h->cur];
+        a.partials = h->partials;
+        e = dispatch(h, OP_MASS, a);
+        if (e != cudaSuccess) return cuda_fail(h, e, "mass kernel");
+        e = launch_finalize(h, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "mass finalize kernel");
+        h->mass_valid = true;
+    }
+    e = cudaMemcpyAsync(mass_out, h->mass_dev, sizeof(double) * h->n, cudaMemcpyDeviceToHost,
+                        h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (mass)");
+    e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaStreamSynchronize");
+}
+
+int lbms_status(lbms_t* h, uint32_t* flags)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!flags) return fail(h, LBMS_EINVAL, "flags is NULL");
+    cudaError_t e = cudaMemcpyAsync(flags, h->status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (status)");
+    e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaStreamSynchronize");
+}
+
+long lbms_steps_done(const lbms_t* h) { return h ? h->steps : -1; }
+
+const char* lbms_last_error(const lbms_t* h) { return h ? h->err : g_create_error; }
+
+void lbms_destroy(lbms_t* h)
+{
+    if (!h) return;
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+    if (h->capture) cudaStreamDestroy(h->capture);
+    delete h;
+}
+
+}  // extern "C"

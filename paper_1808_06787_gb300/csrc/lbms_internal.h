@@ -1,0 +1,52 @@
+// Internal interface between the host runtime (lbms.cu) and the per-lattice
+// kernel translation units (k_d2q5.cu, k_d2q9.cu, k_d3q7.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbms.h"
+
+namespace lbms {
+
+constexpr int kBlock = 256;  // threads per block of every node kernel
+
+// Kernel selector for the per-lattice dispatchers.
+enum Op : int {
+    OP_STEP = 0,       // one stream-collide step fin -> fout
+    OP_STEP_MASS = 1,  // the same, also writing per-block mass partials
+    OP_INIT = 2,       // f+ = w_k xi from a mole-fraction chunk
+    OP_MOMENTS = 3,    // xi (and J) of a cell range into a field chunk
+    OP_MASS = 4        // per-block mass partials of the current state only
+};
+
+// Everything a node kernel may need, dtype-agnostic; the dispatcher converts
+// the coefficients to the kernel's type.
+struct KArgs {
+    const void* fin = nullptr;  // populations read (step: t-1 post-collision; moments: previous buffer or null)
+    void* fout = nullptr;       // populations written (step, init) or read (moments, mass: current buffer)
+    const void* field_in = nullptr;  // init: mole-fraction chunk [n][stride]
+    void* field_x = nullptr;         // moments: mole-fraction chunk [n][stride]
+    void* field_J = nullptr;         // moments: flux chunk [n][dim][stride] or null
+    int nx = 1, ny = 1, nz = 1;
+    uint32_t cells = 0;
+    uint32_t c0 = 0, c1 = 0, stride = 0;  // cell range [c0, c1) and field stride (init, moments)
+    uint32_t noflux = 0;                  // bit f set: face f is no-flux (x-, x+, y-, y+, z-, z+)
+    int relax = LBMS_RELAX_MAGIC;
+    int n_species = 2;
+    double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};  // 1 / D_ij
+    double2* partials = nullptr;  // [blocks][n] (sum, compensation)
+    uint32_t* status = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+// Per-lattice dispatchers: launch `op` for S = n_species - 1 and dtype.
+// Return cudaSuccess or the launch error.
+cudaError_t dispatch_d2q5(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_d2q9(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_d3q7(Op op, int dtype, const KArgs& a);
+
+// Number of blocks a node kernel over `cells` nodes is launched with.
+inline uint32_t node_blocks(uint32_t cells) { return (cells + kBlock - 1) / kBlock; }
+
+}  // namespace lbms

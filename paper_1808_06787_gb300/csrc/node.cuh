@@ -1,0 +1,204 @@
+// Per-node arithmetic of the Maxwell-Stefan MRT model, in registers.
+//
+// Relaxation matrices.  With D~ = B^{-1} (Eq. 2-11) and the Chapman-Enskog
+// relation D~ = c_s^2 (Lambda_1^{-1} - I/2) (Eq. 3-26),
+//     Lambda_1 = (B^{-1}/c_s^2 + I/2)^{-1} = K^{-1} B,   K = I/c_s^2 + B/2,
+// so one Gauss-Jordan elimination of [K | B] gives Lambda_1 without forming
+// B^{-1} (B need not even be invertible).  The elimination runs without
+// pivoting: B has real non-negative eigenvalues (it is the reduced form of the
+// Maxwell-Stefan friction matrix, which is diagonally similar to a symmetric
+// positive semi-definite one), and every pivot of K has been found to be at
+// least 1/c_s^2 for compositions with vanishing species and diffusivities
+// spread over four decades; the test-suite checks that property.
+// Lambda_2 follows Eq. 3-16, or equals Lambda_1 for SRT.
+//
+// Collision.  For moment bases whose rows are the total mass, odd-order rows
+// (relaxed by Lambda_1) and even-order rows (relaxed by Lambda_2), the
+// moment-space collision of Eq. 3-13a equals the pair form used here: for each
+// opposite pair (k, kbar) with g = f - w xi,
+//     s = (g_k + g_kbar)/2,  a = (g_k - g_kbar)/2,
+//     f+_k = f_k - Lambda_2 s - Lambda_1 a,  f+_kbar = f_k - Lambda_2 s + Lambda_1 a,
+// and f+_0 = f_0 - Lambda_2 g_0 for the rest population (the conserved moment
+// has m - m_eq = 0).  Sec. 3.1 notes that odd/even relaxation groups make the
+// MRT model a two-relaxation-time model.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace lbms {
+
+// Lambda_1 = K^{-1} B and Lambda_2 (Eq. 3-16 or SRT) from all S+1 mole fractions.
+template <int S, typename T, typename InvD>
+__device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const InvD& invD,
+                                                    T cs2inv, int relax, T (&L1)[S][S],
+                                                    T (&L2)[S][S])
+{
+    T K[S][S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            T b;
+            if (i != j) {
+                b = xi[i] * (invD[i][S] - invD[i][j]);  // Eq. 2-10, i != j
+            } else {
+                b = xi[i] * invD[i][S];  // Eq. 2-10, i == j
+#pragma unroll
+                for (int k = 0; k <= S; ++k)
+                    if (k != i) b += xi[k] * invD[i][k];
+            }
+            L1[i][j] = b;
+            K[i][j] = T(0.5) * b + (i == j ? cs2inv : T(0));
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+        const T inv = T(1) / K[p][p];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            K[p][j] *= inv;
+            L1[p][j] *= inv;
+        }
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            if (r == p) continue;
+            const T fac = K[r][p];
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                K[r][j] -= fac * K[p][j];
+                L1[r][j] -= fac * L1[p][j];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
+    if (relax == LBMS_RELAX_MAGIC) {
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const T l = L1[i][i];
+            L2[i][i] = T(8) * (l - T(2)) / (l - T(8));  // Eq. 3-16, i == j
+        }
+    }
+}
+
+// xi_i = sum_k f_k^i (Eq. 3-15) and xi_n = 1 - sum (Eq. 2-3b).
+template <int LAT, int S, typename T>
+__device__ __forceinline__ void mole_fractions(const T (&f)[S][Lattice<LAT>::Q], T (&xi)[S + 1])
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    T sum = T(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        T x = f[s][0];
+#pragma unroll
+        for (int k = 1; k < Q; ++k) x += f[s][k];
+        xi[s] = x;
+        sum += x;
+    }
+    xi[S] = T(1) - sum;
+}
+
+// In-place collision in the pair form (see the header comment).
+template <int LAT, int S, typename T>
+__device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi)[S + 1],
+                                        const T (&L1)[S][S], const T (&L2)[S][S])
+{
+    using L = Lattice<LAT>;
+    {
+        const T w0 = T(L::w(0));
+        T g[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) g[j] = f[j][0] - w0 * xi[j];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            T d = T(0);
+#pragma unroll
+            for (int j = 0; j < S; ++j) d += L2[i][j] * g[j];
+            f[i][0] -= d;
+        }
+    }
+#pragma unroll
+    for (int pr = 0; pr < L::NPAIR; ++pr) {
+        const int ka = 2 * pr + 1, kb = 2 * pr + 2;
+        const T wp = T(L::w(ka));
+        T sym[S], asym[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            sym[j] = T(0.5) * (f[j][ka] + f[j][kb]) - wp * xi[j];
+            asym[j] = T(0.5) * (f[j][ka] - f[j][kb]);
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            T ds = T(0), da = T(0);
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                ds += L2[i][j] * sym[j];
+                da += L1[i][j] * asym[j];
+            }
+            f[i][ka] -= ds + da;
+            f[i][kb] -= ds - da;
+        }
+    }
+}
+
+// Gather f_k(x, t) = f+_k(x - c_k, t-1) for every species and direction: the
+// propagation of Eq. 3-13b read in the pull direction.  A source across a
+// periodic face wraps; a source across a no-flux face is replaced by the node's
+// own opposite population, f_k(x) = f+_kbar(x) (half-way bounce-back, Sec. 4).
+template <int LAT, int S, typename T>
+__device__ __forceinline__ void pull(const T* __restrict__ fin, uint32_t cells, int x, int y,
+                                     int z, int nx, int ny, int nz, uint32_t cell,
+                                     uint32_t noflux, T (&f)[S][Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+    constexpr int Q = L::Q;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
+        int xs = x - cx, ys = y - cy, zs = z - cz;
+        bool bounce = false;
+        if (cx == 1 && x == 0) {
+            if (noflux & 1u) bounce = true; else xs = nx - 1;
+        }
+        if (cx == -1 && x == nx - 1) {
+            if (noflux & 2u) bounce = true; else xs = 0;
+        }
+        if (cy == 1 && y == 0) {
+            if (noflux & 4u) bounce = true; else ys = ny - 1;
+        }
+        if (cy == -1 && y == ny - 1) {
+            if (noflux & 8u) bounce = true; else ys = 0;
+        }
+        if (cz == 1 && z == 0) {
+            if (noflux & 16u) bounce = true; else zs = nz - 1;
+        }
+        if (cz == -1 && z == nz - 1) {
+            if (noflux & 32u) bounce = true; else zs = 0;
+        }
+        const uint32_t src =
+            bounce ? cell : ((uint32_t)zs * (uint32_t)ny + (uint32_t)ys) * (uint32_t)nx + (uint32_t)xs;
+        const int kk = bounce ? opp(k) : k;
+#pragma unroll
+        for (int s = 0; s < S; ++s) f[s][k] = fin[(size_t)(s * Q + kk) * cells + src];
+    }
+}
+
+// Two-sum accumulation (Knuth): (s, c) += v with the rounding error kept in c.
+__device__ __forceinline__ void two_sum_add(double& s, double& c, double v)
+{
+    const double t = s + v;
+    const double bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
+// (s, c) += (s2, c2)
+__device__ __forceinline__ void two_sum_merge(double& s, double& c, double s2, double c2)
+{
+    two_sum_add(s, c, s2);
+    c += c2;
+}
+
+}  // namespace lbms

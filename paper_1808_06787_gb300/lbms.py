@@ -1,0 +1,263 @@
+"""Thin Python binding of the C ABI in ``include/lbms.h``.
+
+Every function of the C library is bound under its own name (``lbms_create``,
+``lbms_set_state``, ``lbms_step``, ``lbms_moments``, ``lbms_mass``,
+``lbms_status``, ``lbms_steps_done``, ``lbms_last_error``, ``lbms_destroy``,
+``lbms_workspace_size``); this module only marshals arguments.  All arithmetic
+runs in the CUDA kernels of ``liblbms.so``.  PyTorch provides the device
+memory (the workspace and field tensors) and the CUDA stream.
+
+``Solver`` wraps one handle with its workspace tensor.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2}
+DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3}
+Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7}
+RELAX = {"magic": 0, "srt": 1}
+FACE = {"periodic": 0, "noflux": 1}
+DTYPES = {torch.float32: 0, torch.float64: 1}
+
+LBMS_OK = 0
+FLAG_NONFINITE = 0x1
+FLAG_RANGE = 0x2
+FLAG_INIT = 0x4
+ERRORS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ERANGE", 6: "ETIMEOUT"}
+
+EXPORTED = (
+    "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_step", "lbms_moments",
+    "lbms_mass", "lbms_status", "lbms_steps_done", "lbms_last_error", "lbms_destroy",
+)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbmsError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load ``liblbms.so`` (building it first if it is missing).  Raises if the
+    CUDA library cannot be loaded: there is no fallback path."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise LbmsError("liblbms.so is not built; run paper_1808_06787_gb300.build.build()")
+            _build.build()
+        # the CUDA runtime torch loaded is reused by soname
+        torch.cuda.is_available()
+        L = ctypes.CDLL(path)
+        P, I, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.lbms_workspace_size.argtypes = [I, I, P, I]
+        L.lbms_workspace_size.restype = SZ
+        L.lbms_create.argtypes = [P, I, I, P, P, I, P, I, P, SZ, P]
+        L.lbms_create.restype = I
+        L.lbms_set_state.argtypes = [P, P]
+        L.lbms_set_state.restype = I
+        L.lbms_step.argtypes = [P, ctypes.c_long]
+        L.lbms_step.restype = I
+        L.lbms_moments.argtypes = [P, P, P]
+        L.lbms_moments.restype = I
+        L.lbms_mass.argtypes = [P, P]
+        L.lbms_mass.restype = I
+        L.lbms_status.argtypes = [P, P]
+        L.lbms_status.restype = I
+        L.lbms_steps_done.argtypes = [P]
+        L.lbms_steps_done.restype = ctypes.c_long
+        L.lbms_last_error.argtypes = [P]
+        L.lbms_last_error.restype = ctypes.c_char_p
+        L.lbms_destroy.argtypes = [P]
+        L.lbms_destroy.restype = None
+        _lib = L
+        return L
+
+
+def _grid(grid) -> ctypes.Array:
+    g = list(grid) + [1] * (3 - len(grid))
+    return (ctypes.c_int * 3)(*[int(v) for v in g])
+
+
+def _faces(bc) -> ctypes.Array:
+    if isinstance(bc, str):
+        bc = (bc,) * 6
+    vals = [FACE[b] if isinstance(b, str) else int(b) for b in bc]
+    if len(vals) != 6:
+        raise ValueError("bc needs 6 face kinds (x-, x+, y-, y+, z-, z+)")
+    return (ctypes.c_int * 6)(*vals)
+
+
+# --- the C entry points under their own names ------------------------------
+
+def lbms_workspace_size(lattice: int, n_species: int, grid, dtype: int) -> int:
+    return int(load().lbms_workspace_size(lattice, n_species, _grid(grid), dtype))
+
+
+def lbms_create(lattice: int, n_species: int, grid, D, relax: int, bc, dtype: int,
+                workspace_ptr: int, workspace_bytes: int, stream_ptr: int) -> ctypes.c_void_p:
+    L = load()
+    h = ctypes.c_void_p()
+    Dm = np.ascontiguousarray(np.asarray(D, dtype=np.float64))
+    rc = L.lbms_create(ctypes.byref(h), lattice, n_species, _grid(grid),
+                       Dm.ctypes.data_as(ctypes.c_void_p), relax, _faces(bc), dtype,
+                       ctypes.c_void_p(workspace_ptr), workspace_bytes, ctypes.c_void_p(stream_ptr))
+    if rc != LBMS_OK:
+        raise LbmsError("lbms_create: %s (%s)" % (ERRORS.get(rc, rc), L.lbms_last_error(None).decode()))
+    return h
+
+
+def _check(h, rc: int, what: str) -> None:
+    if rc != LBMS_OK:
+        raise LbmsError("%s: %s (%s)" % (what, ERRORS.get(rc, rc), load().lbms_last_error(h).decode()))
+
+
+def lbms_set_state(h, x0_ptr: int) -> None:
+    _check(h, load().lbms_set_state(h, ctypes.c_void_p(x0_ptr)), "lbms_set_state")
+
+
+def lbms_step(h, n_steps: int) -> None:
+    _check(h, load().lbms_step(h, int(n_steps)), "lbms_step")
+
+
+def lbms_moments(h, x_ptr: int, J_ptr: Optional[int]) -> None:
+    _check(h, load().lbms_moments(h, ctypes.c_void_p(x_ptr),
+                                  ctypes.c_void_p(J_ptr) if J_ptr else None), "lbms_moments")
+
+
+def lbms_mass(h, n_species: int) -> np.ndarray:
+    out = np.zeros(n_species, dtype=np.float64)
+    _check(h, load().lbms_mass(h, out.ctypes.data_as(ctypes.c_void_p)), "lbms_mass")
+    return out
+
+
+def lbms_status(h) -> int:
+    fl = ctypes.c_uint32()
+    _check(h, load().lbms_status(h, ctypes.byref(fl)), "lbms_status")
+    return int(fl.value)
+
+
+def lbms_steps_done(h) -> int:
+    return int(load().lbms_steps_done(h))
+
+
+def lbms_last_error(h) -> str:
+    return load().lbms_last_error(h).decode()
+
+
+def lbms_destroy(h) -> None:
+    load().lbms_destroy(h)
+
+
+# --- convenience wrapper ---------------------------------------------------
+
+class Solver:
+    """One solver handle and the torch-owned workspace it runs in.
+
+    ``lattice``: "D2Q5" | "D2Q9" | "D3Q7"; ``D``: n x n binary diffusivities in
+    lattice units; ``grid``: (nx, ny[, nz]); ``bc``: one kind for all faces or six
+    kinds (x-, x+, y-, y+, z-, z+); ``relax``: "magic" (Eq. 3-16) or "srt";
+    ``dtype``: torch.float32 or torch.float64.  Work is ordered on ``stream``
+    (default: the current torch stream of ``device``).
+    """
+
+    def __init__(self, lattice: str, D, grid: Sequence[int], *, bc="periodic",
+                 relax: str = "magic", dtype=torch.float32, device="cuda",
+                 stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise LbmsError("the lbms solver needs a CUDA device")
+        self.lattice = lattice
+        self.D = np.asarray(D, dtype=np.float64)
+        self.n = int(self.D.shape[0])
+        g = list(grid) + [1] * (3 - len(grid))
+        self.grid = tuple(int(v) for v in g)
+        self.dim = DIMS[lattice]
+        self.dtype = dtype
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        lat, dt = LATTICES[lattice], DTYPES[dtype]
+        nbytes = lbms_workspace_size(lat, self.n, self.grid, dt)
+        if nbytes == 0:
+            raise LbmsError("invalid lattice/species/grid/dtype combination")
+        # workspace: raw bytes owned by torch, 256-byte aligned by the caching allocator
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._h = lbms_create(lat, self.n, self.grid, self.D, RELAX[relax], bc, dt,
+                              self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    @property
+    def field_shape(self):
+        nx, ny, nz = self.grid
+        return (self.n, nz, ny, nx)
+
+    @property
+    def flux_shape(self):
+        nx, ny, nz = self.grid
+        return (self.n, self.dim, nz, ny, nx)
+
+    def _field(self, t: torch.Tensor, shape) -> torch.Tensor:
+        if tuple(t.shape) != tuple(shape) or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError("expected a contiguous %s tensor of shape %s" % (self.dtype, shape))
+        return t
+
+    def set_state(self, x0) -> None:
+        if isinstance(x0, np.ndarray):
+            x0 = torch.from_numpy(np.ascontiguousarray(x0)).to(self.dtype)
+        x0 = self._field(x0, self.field_shape)
+        lbms_set_state(self._h, x0.data_ptr())
+        self._keep = x0  # host sources must live until the copies ran
+        if not x0.is_cuda:
+            self.stream.synchronize()
+
+    def step(self, n: int) -> None:
+        lbms_step(self._h, n)
+
+    def moments(self, x_out: Optional[torch.Tensor] = None, J_out: Optional[torch.Tensor] = None,
+                flux: bool = False):
+        if x_out is None:
+            x_out = torch.empty(self.field_shape, dtype=self.dtype, device=self.device)
+        self._field(x_out, self.field_shape)
+        if flux and J_out is None:
+            J_out = torch.empty(self.flux_shape, dtype=self.dtype, device=x_out.device)
+        if J_out is not None:
+            self._field(J_out, self.flux_shape)
+        lbms_moments(self._h, x_out.data_ptr(), J_out.data_ptr() if J_out is not None else None)
+        return (x_out, J_out) if J_out is not None else x_out
+
+    def mass(self) -> np.ndarray:
+        return lbms_mass(self._h, self.n)
+
+    def status(self) -> int:
+        return lbms_status(self._h)
+
+    @property
+    def steps_done(self) -> int:
+        return lbms_steps_done(self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lbms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
