@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kBlock) k_step(StepParams<T> p)
         check_range<S, T>(xi, p.status);
         T L1[S][S], L2[S][S];
         relaxation_matrices<S, T>(xi, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
-        collide<LAT, S, T>(f, xi, L1, L2);
+        collide<LAT, S, T>(f, xi, L1, L2, cell * 0x27d4eb2du);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
@@ -185,10 +185,19 @@ __global__ void __launch_bounds__(kBlock) k_init(FieldParams<T> p)
         finite &= (bool)isfinite((double)xi[s]);
     }
     if (!finite || !(fabs(sum - 1.0) <= 1e-5)) atomicOr(p.status, LBMS_FLAG_INIT);
+    // moving populations w_k xi; the rest population takes what is left of xi,
+    // so that sum_k f_k = xi up to one rounding whatever the weights round to
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s) {
+        T moving = T(0);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) p.fcur[(size_t)(s * Q + k) * p.cells + cell] = T(L::w(k)) * xi[s];
+        for (int k = 1; k < Q; ++k) {
+            const T fk = T(L::w(k)) * xi[s];
+            moving += fk;
+            p.fcur[(size_t)(s * Q + k) * p.cells + cell] = fk;
+        }
+        p.fcur[(size_t)(s * Q) * p.cells + cell] = xi[s] - moving;
+    }
 }
 
 // Mole fractions at t from the stored post-collision populations (the collision

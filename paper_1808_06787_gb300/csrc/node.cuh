@@ -18,9 +18,23 @@
 // opposite pair (k, kbar) with g = f - w xi,
 //     s = (g_k + g_kbar)/2,  a = (g_k - g_kbar)/2,
 //     f+_k = f_k - Lambda_2 s - Lambda_1 a,  f+_kbar = f_k - Lambda_2 s + Lambda_1 a,
-// and f+_0 = f_0 - Lambda_2 g_0 for the rest population (the conserved moment
-// has m - m_eq = 0).  Sec. 3.1 notes that odd/even relaxation groups make the
-// MRT model a two-relaxation-time model.
+// and for the rest population f+_0 = f_0 - Lambda_2 g_0.  Sec. 3.1 notes that
+// odd/even relaxation groups make the MRT model a two-relaxation-time model.
+//
+// Conservation in finite precision.  The conserved moment has m - m_eq = 0, so
+// in exact arithmetic the collision keeps sum_k f_k of every species at every
+// node, which is what makes f+_0 = f_0 - Lambda_2 g_0 equal to
+//     f+_0 = f_0 + sum_{k != 0} (f_k - f+_k).
+// The kernels use this second form, with the moving populations' increments
+// summed first and added to f_0 by an error-free two-sum, so the node's mass is
+// carried over exactly up to the single final rounding of f+_0.  In FP32 that
+// rounding is stochastic: the two-sum remainder decides, against a uniform
+// number hashed from the value's bits and the node, whether to round up or
+// down, which makes the residual zero-mean and uncorrelated between nodes.
+// Round-to-nearest residuals are not: identical nodes (a field uniform along
+// an axis) and slowly varying states repeat the same residual, and with
+// weights such as 1/9 or 1/36 that do not sum to one in FP32 the plain form
+// loses mass at every node every step.  The results stay deterministic.
 #pragma once
 
 #include "lattice.cuh"
@@ -100,25 +114,49 @@ __device__ __forceinline__ void mole_fractions(const T (&f)[S][Lattice<LAT>::Q],
     xi[S] = T(1) - sum;
 }
 
-// In-place collision in the pair form (see the header comment).
+// Final rounding of the rest population from the exact value hi + lo.
+__device__ __forceinline__ uint32_t mix32(uint32_t h)
+{
+    // finaliser of MurmurHash3 (Appleby): avalanche of a 32-bit key
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ float round_rest(float hi, float lo, uint32_t key)
+{
+    // hi = RN(hi + lo) and |lo| <= half the gap to the neighbour on lo's side;
+    // moving to that neighbour with probability |lo| / gap is unbiased.
+    const uint32_t h = mix32(__float_as_uint(hi) ^ (__float_as_uint(lo) * 0x9e3779b1u) ^ key);
+    const float u = (float)(h >> 8) * 0x1p-24f;
+    const float nb = nextafterf(hi, lo > 0.0f ? INFINITY : -INFINITY);
+    return fabsf(lo) > u * fabsf(nb - hi) ? nb : hi;
+}
+
+__device__ __forceinline__ double round_rest(double hi, double, uint32_t) { return hi; }
+
+// Error-free sum a + b = s + e (Knuth's two-sum).
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
+{
+    s = a + b;
+    const T bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// In-place collision in the pair form (see the header comment); `key` seeds
+// the stochastic rounding of the rest population (FP32 only).
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi)[S + 1],
-                                        const T (&L1)[S][S], const T (&L2)[S][S])
+                                        const T (&L1)[S][S], const T (&L2)[S][S], uint32_t key)
 {
     using L = Lattice<LAT>;
-    {
-        const T w0 = T(L::w(0));
-        T g[S];
+    T moved[S];
 #pragma unroll
-        for (int j = 0; j < S; ++j) g[j] = f[j][0] - w0 * xi[j];
-#pragma unroll
-        for (int i = 0; i < S; ++i) {
-            T d = T(0);
-#pragma unroll
-            for (int j = 0; j < S; ++j) d += L2[i][j] * g[j];
-            f[i][0] -= d;
-        }
-    }
+    for (int i = 0; i < S; ++i) moved[i] = T(0);
 #pragma unroll
     for (int pr = 0; pr < L::NPAIR; ++pr) {
         const int ka = 2 * pr + 1, kb = 2 * pr + 2;
@@ -137,9 +175,19 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
                 ds += L2[i][j] * sym[j];
                 da += L1[i][j] * asym[j];
             }
-            f[i][ka] -= ds + da;
-            f[i][kb] -= ds - da;
+            const T na = f[i][ka] - (ds + da);
+            const T nb = f[i][kb] - (ds - da);
+            moved[i] += (f[i][ka] - na) + (f[i][kb] - nb);
+            f[i][ka] = na;
+            f[i][kb] = nb;
         }
+    }
+    // rest population: f+_0 = f_0 + sum_{k != 0} (f_k - f+_k)
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        T hi, lo;
+        two_sum(f[i][0], moved[i], hi, lo);
+        f[i][0] = round_rest(hi, lo, key ^ (0x165667b1u * (uint32_t)(i + 1)));
     }
 }
 
