@@ -84,9 +84,9 @@ enum {
 
 /*
  * Bytes of device workspace that lbms_create needs for this problem: two
- * population buffers of S * Q * cells elements (ping-pong), per-block FP64
- * partial sums for the mass diagnostic, a status word and a staging area for
- * host input/output.  Returns 0 for an invalid combination.
+ * population buffers of S * Q * cells elements (ping-pong), per-block partial
+ * sums for the mass diagnostic, a status word and a staging area (at most
+ * 16 MiB) for host input/output.  Returns 0 for an invalid combination.
  */
 size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dtype);
 
@@ -130,9 +130,9 @@ int lbms_set_state(lbms_t* h, const void* x0);
 /*
  * Advance n_steps >= 0 time steps of Eqs. 3-13a/3-13b (pull form: each node
  * gathers f+_k(x - c_k), collides, and stores its post-collision populations).
- * The last step of each call also writes per-block FP64 partial sums of every
- * species' mole fraction and reduces them, so lbms_mass after lbms_step reads
- * no populations.  Asynchronous: launch errors are returned at once, numerical
+ * The last step of each call also writes per-block partial sums of every
+ * species' mole fraction and reduces them (see lbms_mass), so lbms_mass after
+ * lbms_step reads no populations.  Asynchronous: launch errors are returned at once, numerical
  * trouble is raised in the status flags.
  */
 int lbms_step(lbms_t* h, long n_steps);
@@ -151,9 +151,12 @@ int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma);
 
 /*
  * Total amount of each species, mass_out[i] = sum over nodes of xi_i, for all n
- * species, in FP64 with compensated (two-sum) accumulation in a fixed order, so
- * that repeated calls on the same state agree bit for bit.  mass_out is a host
- * array of n doubles.  Synchronises the stream.
+ * species (xi of Eq. 3-15, xi_n by Eq. 2-3b).  FP32 solvers add every node's
+ * value as a 64-bit fixed-point number with 2^-k resolution, k = 59 - ceil(log2
+ * cells) clamped to [8, 40] (k = 35 for 256^3 nodes), which makes the sum exact
+ * and independent of order; FP64 solvers use two-sum compensated FP64
+ * accumulation in a fixed order.  Repeated calls on the same state agree bit
+ * for bit.  mass_out is a host array of n doubles.  Synchronises the stream.
  */
 int lbms_mass(lbms_t* h, double* mass_out);
 

@@ -15,26 +15,24 @@ struct Coeffs {
     T invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES];
 };
 
+// Mass partials.  FP32 solvers accumulate each node's mole fraction as a signed
+// 64-bit fixed-point number xi * 2^shift (exact integer sums, independent of
+// order); FP64 solvers use FP64 two-sum pairs.  Both reduce in a fixed order.
+struct MassOut {
+    void* partials;  // [blocks][S + 1] of int64 (FP32) or double2 (FP64)
+    int shift;       // fixed-point fraction bits (FP32)
+};
+
 template <typename T>
 struct StepParams {
     const T* __restrict__ fin;
     T* __restrict__ fout;
-    int nx, ny, nz;
-    uint32_t cells;
-    uint32_t noflux;
+    Geom g;
     int relax;
-    double2* partials;  // [blocks][S + 1] when mass partials are requested
+    MassOut mass;
     uint32_t* status;
     Coeffs<T> co;
 };
-
-__device__ __forceinline__ void node_coords(uint32_t cell, int nx, int ny, int& x, int& y, int& z)
-{
-    const uint32_t row = cell / (uint32_t)nx;
-    x = (int)(cell - row * (uint32_t)nx);
-    z = (int)(row / (uint32_t)ny);
-    y = (int)(row - (uint32_t)z * (uint32_t)ny);
-}
 
 // Raise the status flags for mole fractions that are non-finite or far
 // outside [0, 1]; the comparison is false for NaN, so one test covers both.
@@ -52,8 +50,24 @@ __device__ __forceinline__ void check_range(const T (&xi)[S + 1], uint32_t* stat
     }
 }
 
-// Block-wide fixed-order reduction of one (sum, compensation) pair per thread;
-// thread 0 returns the block total.  All threads of the block must call it.
+// Block-wide fixed-order reductions; thread 0 receives the block total.  All
+// threads of the block must call these.
+__device__ __forceinline__ long long block_reduce_fixed(long long v, long long* smem)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? smem[lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    }
+    __syncthreads();
+    return v;
+}
+
 __device__ __forceinline__ void block_reduce_pair(double& s, double& c, double2* smem)
 {
 #pragma unroll
@@ -79,16 +93,34 @@ __device__ __forceinline__ void block_reduce_pair(double& s, double& c, double2*
     __syncthreads();
 }
 
-// Per-block partial sums of the n = S + 1 mole fractions held by the threads.
+// Per-block partial sums of the n = S + 1 mole fractions (zero for idle threads).
 template <int S>
-__device__ __forceinline__ void write_mass_partials(const double (&v)[S + 1], double2* partials)
+__device__ __forceinline__ void write_mass_partials(const float (&xi)[S + 1], bool active,
+                                                    const MassOut& m)
 {
-    __shared__ double2 red[kBlock / 32];
+    __shared__ long long red[kBlock / 32];
+    const float scale = __int_as_float((127 + m.shift) << 23);  // 2^shift, exact
+    long long* out = static_cast<long long*>(m.partials);
 #pragma unroll
     for (int s = 0; s <= S; ++s) {
-        double sum = v[s], comp = 0.0;
+        // |xi| beyond 4 (already flagged) is clipped so that sums cannot overflow
+        const float v = active ? fminf(fmaxf(xi[s], -4.0f), 4.0f) : 0.0f;
+        const long long q = block_reduce_fixed(__float2ll_rn(v * scale), red);
+        if (threadIdx.x == 0) out[(size_t)blockIdx.x * (S + 1) + s] = q;
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void write_mass_partials(const double (&xi)[S + 1], bool active,
+                                                    const MassOut& m)
+{
+    __shared__ double2 red[kBlock / 32];
+    double2* out = static_cast<double2*>(m.partials);
+#pragma unroll
+    for (int s = 0; s <= S; ++s) {
+        double sum = active ? xi[s] : 0.0, comp = 0.0;
         block_reduce_pair(sum, comp, red);
-        if (threadIdx.x == 0) partials[(size_t)blockIdx.x * (S + 1) + s] = make_double2(sum, comp);
+        if (threadIdx.x == 0) out[(size_t)blockIdx.x * (S + 1) + s] = make_double2(sum, comp);
     }
 }
 
@@ -101,13 +133,12 @@ __global__ void __launch_bounds__(kBlock) k_step(StepParams<T> p)
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
-    const bool active = cell < p.cells;
+    const bool active = cell < p.g.cells;
     T xi[S + 1];
     if (active) {
-        int x, y, z;
-        node_coords(cell, p.nx, p.ny, x, y, z);
+        const Neighbourhood h = neighbourhood(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, p.cells, x, y, z, p.nx, p.ny, p.nz, cell, p.noflux, f);
+        pull<LAT, S, T>(p.fin, p.g, cell, h, f);
         mole_fractions<LAT, S, T>(f, xi);
         check_range<S, T>(xi, p.status);
         T L1[S][S], L2[S][S];
@@ -116,14 +147,9 @@ __global__ void __launch_bounds__(kBlock) k_step(StepParams<T> p)
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.cells + cell] = f[s][k];
+            for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.g.cells + cell] = f[s][k];
     }
-    if (MASS) {
-        double v[S + 1];
-#pragma unroll
-        for (int s = 0; s <= S; ++s) v[s] = active ? (double)xi[s] : 0.0;
-        write_mass_partials<S>(v, p.partials);
-    }
+    if (MASS) write_mass_partials<S>(xi, active, p.mass);
 }
 
 // Mass partials of the current (post-collision) state without stepping.
@@ -132,22 +158,17 @@ __global__ void __launch_bounds__(kBlock) k_mass(StepParams<T> p)
 {
     constexpr int Q = Lattice<LAT>::Q;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
-    double v[S + 1];
-    if (cell < p.cells) {
+    const bool active = cell < p.g.cells;
+    T xi[S + 1];
+    if (active) {
         T f[S][Q];
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int k = 0; k < Q; ++k) f[s][k] = p.fout[(size_t)(s * Q + k) * p.cells + cell];
-        T xi[S + 1];
+            for (int k = 0; k < Q; ++k) f[s][k] = p.fout[(size_t)(s * Q + k) * p.g.cells + cell];
         mole_fractions<LAT, S, T>(f, xi);
-#pragma unroll
-        for (int s = 0; s <= S; ++s) v[s] = (double)xi[s];
-    } else {
-#pragma unroll
-        for (int s = 0; s <= S; ++s) v[s] = 0.0;
     }
-    write_mass_partials<S>(v, p.partials);
+    write_mass_partials<S>(xi, active, p.mass);
 }
 
 template <typename T>
@@ -157,9 +178,8 @@ struct FieldParams {
     const T* x_in;    // init: [S+1][stride]
     T* x_out;         // moments: [S+1][stride]
     T* J_out;         // moments: [S+1][dim][stride] or null
-    int nx, ny, nz;
-    uint32_t cells, c0, c1, stride;
-    uint32_t noflux;
+    Geom g;
+    uint32_t c0, c1, stride;
     int relax;
     uint32_t* status;
     Coeffs<T> co;
@@ -194,9 +214,9 @@ __global__ void __launch_bounds__(kBlock) k_init(FieldParams<T> p)
         for (int k = 1; k < Q; ++k) {
             const T fk = T(L::w(k)) * xi[s];
             moving += fk;
-            p.fcur[(size_t)(s * Q + k) * p.cells + cell] = fk;
+            p.fcur[(size_t)(s * Q + k) * p.g.cells + cell] = fk;
         }
-        p.fcur[(size_t)(s * Q) * p.cells + cell] = xi[s] - moving;
+        p.fcur[(size_t)(s * Q) * p.g.cells + cell] = xi[s] - moving;
     }
 }
 
@@ -217,7 +237,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int k = 0; k < Q; ++k) f[s][k] = p.fcur[(size_t)(s * Q + k) * p.cells + cell];
+            for (int k = 0; k < Q; ++k) f[s][k] = p.fcur[(size_t)(s * Q + k) * p.g.cells + cell];
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
 #pragma unroll
@@ -230,10 +250,9 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
 #pragma unroll
         for (int a = 0; a < DIM; ++a) J[s][a] = T(0);
     if (p.fprev) {
-        int x, y, z;
-        node_coords(cell, p.nx, p.ny, x, y, z);
+        const Neighbourhood h = neighbourhood(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fprev, p.cells, x, y, z, p.nx, p.ny, p.nz, cell, p.noflux, f);
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, f);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         T L1[S][S], L2[S][S];
@@ -278,6 +297,28 @@ Coeffs<T> make_coeffs(const KArgs& a)
     return c;
 }
 
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.s = 31 + l;
+    f.m = ((1ull << f.s) + d - 1) / d;
+    return f;
+}
+
+inline Geom make_geom(const KArgs& a)
+{
+    Geom g;
+    g.nx = a.nx; g.ny = a.ny; g.nz = a.nz;
+    g.nxy = (uint32_t)a.nx * (uint32_t)a.ny;
+    g.cells = a.cells;
+    g.noflux = a.noflux;
+    g.dnx = make_fastdiv((uint32_t)a.nx);
+    g.dny = make_fastdiv((uint32_t)a.ny);
+    return g;
+}
+
 template <int LAT, int S, typename T>
 cudaError_t launch(Op op, const KArgs& a)
 {
@@ -285,11 +326,10 @@ cudaError_t launch(Op op, const KArgs& a)
         StepParams<T> p;
         p.fin = static_cast<const T*>(a.fin);
         p.fout = static_cast<T*>(a.fout);
-        p.nx = a.nx; p.ny = a.ny; p.nz = a.nz;
-        p.cells = a.cells;
-        p.noflux = a.noflux;
+        p.g = make_geom(a);
         p.relax = a.relax;
-        p.partials = a.partials;
+        p.mass.partials = a.partials;
+        p.mass.shift = a.fixed_shift;
         p.status = a.status;
         p.co = make_coeffs<T>(a);
         const uint32_t blocks = node_blocks(a.cells);
@@ -307,10 +347,8 @@ cudaError_t launch(Op op, const KArgs& a)
     p.x_in = static_cast<const T*>(a.field_in);
     p.x_out = static_cast<T*>(a.field_x);
     p.J_out = static_cast<T*>(a.field_J);
-    p.nx = a.nx; p.ny = a.ny; p.nz = a.nz;
-    p.cells = a.cells;
+    p.g = make_geom(a);
     p.c0 = a.c0; p.c1 = a.c1; p.stride = a.stride;
-    p.noflux = a.noflux;
     p.relax = a.relax;
     p.status = a.status;
     p.co = make_coeffs<T>(a);

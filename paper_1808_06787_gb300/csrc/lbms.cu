@@ -1,6 +1,6 @@
 // Host runtime behind the C ABI of include/lbms.h: argument checks, workspace
 // layout, ping-pong buffers, CUDA-graph replay of step runs, host staging and
-// the deterministic FP64 mass reduction.
+// the deterministic mass reduction.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -58,8 +58,31 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
 
 thread_local char g_create_error[256] = "";
 
-__global__ void k_mass_finalize(const double2* __restrict__ partials, uint32_t blocks, int n,
-                                double* __restrict__ out)
+// Final fixed-order reduction of the per-block mass partials, one block per
+// species.  FP32 solvers: exact int64 fixed-point sums scaled by 2^-shift.
+__global__ void k_mass_finalize_fixed(const long long* __restrict__ partials, uint32_t blocks, int n,
+                                      int shift, double* __restrict__ out)
+{
+    __shared__ long long red[kBlock / 32];
+    const int s = blockIdx.x;
+    long long acc = 0;
+    for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x) acc += partials[(size_t)b * n + s];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) out[s] = ldexp((double)acc, -shift);
+    }
+}
+
+// FP64 solvers: two-sum pairs merged in a fixed order.
+__global__ void k_mass_finalize_pairs(const double2* __restrict__ partials, uint32_t blocks, int n,
+                                      double* __restrict__ out)
 {
     __shared__ double2 red[kBlock / 32];
     const int s = blockIdx.x;
@@ -68,7 +91,6 @@ __global__ void k_mass_finalize(const double2* __restrict__ partials, uint32_t b
         const double2 v = partials[(size_t)b * n + s];
         two_sum_merge(sum, comp, v.x, v.y);
     }
-    // same fixed-order block reduction as the step kernel
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double s2 = __shfl_down_sync(0xffffffffu, sum, off);
@@ -91,6 +113,16 @@ __global__ void k_mass_finalize(const double2* __restrict__ partials, uint32_t b
     }
 }
 
+// Fraction bits of the fixed-point mass partials: the sum of |xi| <= 4 over all
+// nodes must stay below 2^62.
+int fixed_shift_for(uint32_t cells)
+{
+    int l = 0;
+    while ((1ull << l) < cells) ++l;
+    int k = 62 - l - 3;
+    return k > 40 ? 40 : (k < 8 ? 8 : k);
+}
+
 }  // namespace
 
 struct lbms_s {
@@ -104,7 +136,8 @@ struct lbms_s {
     Layout lay{};
     void* f[2] = {nullptr, nullptr};
     int cur = 0;  // f[cur] holds the post-collision populations at time t
-    double2* partials = nullptr;
+    void* partials = nullptr;
+    int fixed_shift = 32;
     double* mass_dev = nullptr;
     bool mass_valid = false;
     uint32_t* status = nullptr;
@@ -154,6 +187,7 @@ KArgs base_args(const lbms_t* h, cudaStream_t st)
     a.n_species = h->n;
     memcpy(a.invD, h->invD, sizeof(a.invD));
     a.status = h->status;
+    a.fixed_shift = h->fixed_shift;
     a.stream = st;
     return a;
 }
@@ -170,7 +204,12 @@ cudaError_t launch_step(const lbms_t* h, int src, bool mass, cudaStream_t st)
 
 cudaError_t launch_finalize(const lbms_t* h, cudaStream_t st)
 {
-    k_mass_finalize<<<h->n, kBlock, 0, st>>>(h->partials, h->blocks, h->n, h->mass_dev);
+    if (h->dtype == LBMS_F32)
+        k_mass_finalize_fixed<<<h->n, kBlock, 0, st>>>(static_cast<const long long*>(h->partials),
+                                                         h->blocks, h->n, h->fixed_shift, h->mass_dev);
+    else
+        k_mass_finalize_pairs<<<h->n, kBlock, 0, st>>>(static_cast<const double2*>(h->partials),
+                                                         h->blocks, h->n, h->mass_dev);
     return cudaGetLastError();
 }
 
@@ -277,7 +316,8 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->lay = L;
     h->f[0] = h->ws + L.off_f0;
     h->f[1] = h->ws + L.off_f1;
-    h->partials = reinterpret_cast<double2*>(h->ws + L.off_partials);
+    h->partials = h->ws + L.off_partials;
+    h->fixed_shift = fixed_shift_for(h->cells);
     h->mass_dev = reinterpret_cast<double*>(h->ws + L.off_mass);
     h->status = reinterpret_cast<uint32_t*>(h->ws + L.off_status);
     h->staging = h->ws + L.off_staging;

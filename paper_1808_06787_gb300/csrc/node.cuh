@@ -41,6 +41,11 @@
 
 namespace lbms {
 
+// Reciprocal used by the per-node solve: the fast hardware approximation in
+// FP32 (well inside the FP32 tolerance), the IEEE division in FP64.
+__device__ __forceinline__ float recip(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+
 // Lambda_1 = K^{-1} B and Lambda_2 (Eq. 3-16 or SRT) from all S+1 mole fractions.
 template <int S, typename T, typename InvD>
 __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const InvD& invD,
@@ -67,7 +72,7 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
     }
 #pragma unroll
     for (int p = 0; p < S; ++p) {
-        const T inv = T(1) / K[p][p];
+        const T inv = recip(K[p][p]);
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             K[p][j] *= inv;
@@ -92,7 +97,7 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
 #pragma unroll
         for (int i = 0; i < S; ++i) {
             const T l = L1[i][i];
-            L2[i][i] = T(8) * (l - T(2)) / (l - T(8));  // Eq. 3-16, i == j
+            L2[i][i] = T(8) * (l - T(2)) * recip(l - T(8));  // Eq. 3-16, i == j
         }
     }
 }
@@ -130,10 +135,13 @@ __device__ __forceinline__ float round_rest(float hi, float lo, uint32_t key)
 {
     // hi = RN(hi + lo) and |lo| <= half the gap to the neighbour on lo's side;
     // moving to that neighbour with probability |lo| / gap is unbiased.
+    // (lo != 0 implies hi != 0; the neighbour of a finite non-zero float on the
+    // side of lo is one step of its bit pattern away from or toward zero)
     const uint32_t h = mix32(__float_as_uint(hi) ^ (__float_as_uint(lo) * 0x9e3779b1u) ^ key);
     const float u = (float)(h >> 8) * 0x1p-24f;
-    const float nb = nextafterf(hi, lo > 0.0f ? INFINITY : -INFINITY);
-    return fabsf(lo) > u * fabsf(nb - hi) ? nb : hi;
+    const int step = ((lo > 0.0f) == (hi > 0.0f)) ? 1 : -1;
+    const float nb = __int_as_float(__float_as_int(hi) + step);
+    return (lo != 0.0f && fabsf(lo) > u * fabsf(nb - hi)) ? nb : hi;
 }
 
 __device__ __forceinline__ double round_rest(double hi, double, uint32_t) { return hi; }
@@ -191,45 +199,79 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
     }
 }
 
+// Grid geometry shared by the node kernels.  Coordinates of a linear node
+// index come from multiply-shift division by the invariant extents nx and ny
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): for n < 2^31 and d < 2^31, with s = 31 + ceil(log2 d)
+// and m = ceil(2^s / d), floor(n / d) = (n * m) >> s exactly.
+struct FastDiv {
+    uint64_t m;
+    uint32_t s;
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return (uint32_t)(((uint64_t)n * m) >> s); }
+};
+
+struct Geom {
+    int nx, ny, nz;
+    uint32_t nxy, cells;
+    uint32_t noflux;  // bit f set: face f is no-flux (x-, x+, y-, y+, z-, z+)
+    FastDiv dnx, dny;
+};
+
+// Source offsets (in nodes) of the gather along each axis for c = +1 and c = -1,
+// with periodic wrap, and whether that source lies across a no-flux face.
+struct Neighbourhood {
+    int32_t ox[2], oy[2], oz[2];  // [0]: c = +1 (source at -1), [1]: c = -1 (source at +1)
+    bool bx[2], by[2], bz[2];
+};
+
+__device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t cell)
+{
+    const uint32_t row = g.dnx.div(cell);
+    const int x = (int)(cell - row * (uint32_t)g.nx);
+    const int z = (int)g.dny.div(row);
+    const int y = (int)(row - (uint32_t)z * (uint32_t)g.ny);
+    Neighbourhood h;
+    const bool xlo = x == 0, xhi = x == g.nx - 1;
+    const bool ylo = y == 0, yhi = y == g.ny - 1;
+    const bool zlo = z == 0, zhi = z == g.nz - 1;
+    const int32_t sx = 1, sy = g.nx, sz = (int32_t)g.nxy;
+    h.ox[0] = xlo ? sx * (g.nx - 1) : -sx;
+    h.ox[1] = xhi ? -sx * (g.nx - 1) : sx;
+    h.oy[0] = ylo ? sy * (g.ny - 1) : -sy;
+    h.oy[1] = yhi ? -sy * (g.ny - 1) : sy;
+    h.oz[0] = zlo ? sz * (g.nz - 1) : -sz;
+    h.oz[1] = zhi ? -sz * (g.nz - 1) : sz;
+    h.bx[0] = xlo && (g.noflux & 1u);
+    h.bx[1] = xhi && (g.noflux & 2u);
+    h.by[0] = ylo && (g.noflux & 4u);
+    h.by[1] = yhi && (g.noflux & 8u);
+    h.bz[0] = zlo && (g.noflux & 16u);
+    h.bz[1] = zhi && (g.noflux & 32u);
+    return h;
+}
+
 // Gather f_k(x, t) = f+_k(x - c_k, t-1) for every species and direction: the
 // propagation of Eq. 3-13b read in the pull direction.  A source across a
 // periodic face wraps; a source across a no-flux face is replaced by the node's
 // own opposite population, f_k(x) = f+_kbar(x) (half-way bounce-back, Sec. 4).
 template <int LAT, int S, typename T>
-__device__ __forceinline__ void pull(const T* __restrict__ fin, uint32_t cells, int x, int y,
-                                     int z, int nx, int ny, int nz, uint32_t cell,
-                                     uint32_t noflux, T (&f)[S][Lattice<LAT>::Q])
+__device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, uint32_t cell,
+                                     const Neighbourhood& h, T (&f)[S][Lattice<LAT>::Q])
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
-        int xs = x - cx, ys = y - cy, zs = z - cz;
+        int32_t off = 0;
         bool bounce = false;
-        if (cx == 1 && x == 0) {
-            if (noflux & 1u) bounce = true; else xs = nx - 1;
-        }
-        if (cx == -1 && x == nx - 1) {
-            if (noflux & 2u) bounce = true; else xs = 0;
-        }
-        if (cy == 1 && y == 0) {
-            if (noflux & 4u) bounce = true; else ys = ny - 1;
-        }
-        if (cy == -1 && y == ny - 1) {
-            if (noflux & 8u) bounce = true; else ys = 0;
-        }
-        if (cz == 1 && z == 0) {
-            if (noflux & 16u) bounce = true; else zs = nz - 1;
-        }
-        if (cz == -1 && z == nz - 1) {
-            if (noflux & 32u) bounce = true; else zs = 0;
-        }
-        const uint32_t src =
-            bounce ? cell : ((uint32_t)zs * (uint32_t)ny + (uint32_t)ys) * (uint32_t)nx + (uint32_t)xs;
-        const int kk = bounce ? opp(k) : k;
+        if (cx != 0) { off += h.ox[cx > 0 ? 0 : 1]; bounce |= h.bx[cx > 0 ? 0 : 1]; }
+        if (cy != 0) { off += h.oy[cy > 0 ? 0 : 1]; bounce |= h.by[cy > 0 ? 0 : 1]; }
+        if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
+        const uint32_t src = bounce ? cell : (uint32_t)((int32_t)cell + off);
+        const size_t plane = (size_t)(bounce ? opp(k) : k) * g.cells;
 #pragma unroll
-        for (int s = 0; s < S; ++s) f[s][k] = fin[(size_t)(s * Q + kk) * cells + src];
+        for (int s = 0; s < S; ++s) f[s][k] = fin[(size_t)s * Q * g.cells + plane + src];
     }
 }
 

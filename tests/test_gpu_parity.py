@@ -267,6 +267,27 @@ def test_mass_matches_field_sum():
     np.testing.assert_allclose(m_fused, m_init, rtol=1e-12)
 
 
+def test_mass_fp32_fixed_point_is_exact_to_its_resolution():
+    """FP32 masses are exact sums of the nodes' values rounded to 2^-k, so they
+    match an FP64 sum of the FP32 moments within cells * 2^-(k+1)."""
+    from paper_1808_06787_gb300 import Solver
+
+    D = sy.random_D(4, seed=21)
+    x0 = sy.gaussian_blobs(4, 512, 384, sigma=20, seed=22)
+    s = Solver("D2Q9", D, (512, 384), bc=(P, P, W, W, P, P))
+    s.set_state(torch.from_numpy(x0).float().cuda())
+    cells = 512 * 384
+    k = 59 - math.ceil(math.log2(cells))
+    for steps in (0, 37):
+        s.step(steps)
+        m = s.mass()
+        x = s.moments().double()
+        # the mass uses xi = sum_k f_k; the moments kernel computes the same sums
+        ref = x.sum(dim=(1, 2, 3)).cpu().numpy()
+        assert np.all(np.abs(m - ref) <= cells * 2.0 ** -(k + 1) + 1e-9 * np.abs(ref))
+        assert np.array_equal(s.mass(), m)
+
+
 def test_status_flags():
     from paper_1808_06787_gb300 import Solver, lbms
 
