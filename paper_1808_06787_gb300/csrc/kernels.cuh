@@ -31,6 +31,11 @@ struct StepParams {
     int relax;
     MassOut mass;
     uint32_t* status;
+    // step counter: read from clock_in, written (+1) to clock_out; the two
+    // words alternate with the population buffers, so replays of a captured
+    // graph see the true step count
+    const uint32_t* clock_in;
+    uint32_t* clock_out;
     Coeffs<T> co;
 };
 
@@ -134,6 +139,8 @@ __global__ void __launch_bounds__(kBlock) k_step(StepParams<T> p)
     constexpr int Q = L::Q;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
     const bool active = cell < p.g.cells;
+    const uint32_t step = *p.clock_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.clock_out = step + 1;
     T xi[S + 1];
     if (active) {
         const Neighbourhood h = neighbourhood(p.g, cell);
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_step(StepParams<T> p)
         check_range<S, T>(xi, p.status);
         T L1[S][S], L2[S][S];
         relaxation_matrices<S, T>(xi, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
-        collide<LAT, S, T>(f, xi, L1, L2, cell * 0x27d4eb2du);
+        collide<LAT, S, T>(f, xi, L1, L2, mix32(step * 0x9e3779b9u) ^ (cell * 0x27d4eb2du));
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
@@ -331,6 +338,8 @@ cudaError_t launch(Op op, const KArgs& a)
         p.mass.partials = a.partials;
         p.mass.shift = a.fixed_shift;
         p.status = a.status;
+        p.clock_in = a.clock_in;
+        p.clock_out = a.clock_out;
         p.co = make_coeffs<T>(a);
         const uint32_t blocks = node_blocks(a.cells);
         if (op == OP_STEP)

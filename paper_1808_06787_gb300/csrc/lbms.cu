@@ -141,6 +141,7 @@ struct lbms_s {
     double* mass_dev = nullptr;
     bool mass_valid = false;
     uint32_t* status = nullptr;
+    uint32_t* clock = nullptr;  // two step-counter words after the status word
     char* staging = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
@@ -199,6 +200,8 @@ cudaError_t launch_step(const lbms_t* h, int src, bool mass, cudaStream_t st)
     a.fin = h->f[src];
     a.fout = h->f[1 - src];
     a.partials = h->partials;
+    a.clock_in = h->clock + src;
+    a.clock_out = h->clock + (1 - src);
     return dispatch(h, mass ? OP_STEP_MASS : OP_STEP, a);
 }
 
@@ -320,6 +323,7 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->fixed_shift = fixed_shift_for(h->cells);
     h->mass_dev = reinterpret_cast<double*>(h->ws + L.off_mass);
     h->status = reinterpret_cast<uint32_t*>(h->ws + L.off_status);
+    h->clock = h->status + 16;
     h->staging = h->ws + L.off_staging;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
@@ -343,6 +347,7 @@ int lbms_set_state(lbms_t* h, const void* x0)
     if (!x0) return fail(h, LBMS_EINVAL, "x0 is NULL");
     h->err[0] = '\0';
     cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->clock, 0, 2 * sizeof(uint32_t), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     h->cur = 0;
     h->steps = 0;

@@ -38,6 +38,8 @@ struct KArgs {
     void* partials = nullptr;  // [blocks][n]: int64 fixed point (FP32) or double2 (FP64)
     int fixed_shift = 32;      // fraction bits of the FP32 fixed-point mass partials
     uint32_t* status = nullptr;
+    const uint32_t* clock_in = nullptr;  // step counter read by a step
+    uint32_t* clock_out = nullptr;       // step counter written by a step
     cudaStream_t stream = nullptr;
 };
 

@@ -30,11 +30,15 @@
 // carried over exactly up to the single final rounding of f+_0.  In FP32 that
 // rounding is stochastic: the two-sum remainder decides, against a uniform
 // number hashed from the value's bits and the node, whether to round up or
-// down, which makes the residual zero-mean and uncorrelated between nodes.
-// Round-to-nearest residuals are not: identical nodes (a field uniform along
-// an axis) and slowly varying states repeat the same residual, and with
-// weights such as 1/9 or 1/36 that do not sum to one in FP32 the plain form
-// loses mass at every node every step.  The results stay deterministic.
+// down, against a uniform number hashed from the node, the species and the
+// step count, which makes the residual zero-mean and uncorrelated between
+// nodes and between steps.  Round-to-nearest residuals are not: identical
+// nodes (a field uniform along an axis) and slowly varying states repeat the
+// same residual, and with weights such as 1/9 or 1/36 that do not sum to one in
+// FP32 the plain form loses mass at every node every step.  (A hash of the
+// state's own bits is not enough either: where the state changes below FP32
+// resolution for many steps, the same decision repeats.)  Results stay
+// deterministic: the step count is a device counter advanced by every step.
 #pragma once
 
 #include "lattice.cuh"
@@ -137,7 +141,7 @@ __device__ __forceinline__ float round_rest(float hi, float lo, uint32_t key)
     // moving to that neighbour with probability |lo| / gap is unbiased.
     // (lo != 0 implies hi != 0; the neighbour of a finite non-zero float on the
     // side of lo is one step of its bit pattern away from or toward zero)
-    const uint32_t h = mix32(__float_as_uint(hi) ^ (__float_as_uint(lo) * 0x9e3779b1u) ^ key);
+    const uint32_t h = mix32(key);
     const float u = (float)(h >> 8) * 0x1p-24f;
     const int step = ((lo > 0.0f) == (hi > 0.0f)) ? 1 : -1;
     const float nb = __int_as_float(__float_as_int(hi) + step);
@@ -155,13 +159,16 @@ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
     e = (a - (s - bp)) + (b - bp);
 }
 
-// In-place collision in the pair form (see the header comment); `key` seeds
-// the stochastic rounding of the rest population (FP32 only).
+// In-place collision in the pair form (see the header comment); `key` (distinct
+// per node and step) seeds the stochastic rounding of the rest population
+// (FP32 only).
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi)[S + 1],
                                         const T (&L1)[S][S], const T (&L2)[S][S], uint32_t key)
 {
     using L = Lattice<LAT>;
+    // sum of the moving populations' increments f_k - f+_k (each exact: f+_k is
+    // within a factor two of f_k); its rounding is far below an ulp of f_0
     T moved[S];
 #pragma unroll
     for (int i = 0; i < S; ++i) moved[i] = T(0);
@@ -195,7 +202,7 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
     for (int i = 0; i < S; ++i) {
         T hi, lo;
         two_sum(f[i][0], moved[i], hi, lo);
-        f[i][0] = round_rest(hi, lo, key ^ (0x165667b1u * (uint32_t)(i + 1)));
+        f[i][0] = round_rest(hi, lo, key + 0x165667b1u * (uint32_t)i);
     }
 }
 
