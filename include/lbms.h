@@ -160,6 +160,38 @@ int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma);
  */
 int lbms_mass(lbms_t* h, double* mass_out);
 
+/*
+ * Species totals of a population field without a handle, a workspace or any
+ * device allocation.  The paper has no counterpart: this is a service entry
+ * point for callers that cannot call cudaMalloc -- code running while a stream
+ * is being captured into a CUDA graph (an allocation would invalidate the
+ * capture), real-time loops whose device memory is fixed at start-up, and
+ * plug-ins whose device memory belongs to a host framework's pool.
+ *   lattice, n_species, grid, dtype  as for lbms_create.
+ *   populations  device buffer of S * Q * cells elements of dtype, laid out
+ *                [s][k][z][y][x] (the layout of a solver's population buffers:
+ *                a solver's state after t steps starts at byte offset
+ *                (t mod 2) * round_up(S * Q * cells * sizeof(dtype), 256) of its
+ *                workspace).  Read only.
+ *   mass_out     n doubles, host or device: sum over nodes of xi_i = sum_k f_k^i
+ *                for the n - 1 evolved species and of the closure species, with
+ *                the reduction lbms_mass uses (bit-identical to lbms_mass right
+ *                after lbms_set_state).
+ *   cuda_stream  stream the work is ordered on; a host mass_out synchronises it.
+ * The per-block partial sums go to a file-scope device array of 4 MiB that
+ * every GPU which loads the library keeps until the process exits; grids whose
+ * partials do not fit (cells * n_species * 8 bytes for F32, * 16 for F64, above
+ * 4 MiB - 256 B, i.e. about 67 M node-species in F32) are rejected with
+ * LBMS_EINVAL and a message in lbms_last_error(NULL).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and every call overwrites the slots it reads, so calls
+ * that overlap on the GPU (other streams, other host threads) race.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ */
+int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], int dtype,
+                      const void* populations, double* mass_out, void* cuda_stream);
+
 /* OR of the status flags raised since lbms_set_state.  Synchronises the stream. */
 int lbms_status(lbms_t* h, uint32_t* flags);
 

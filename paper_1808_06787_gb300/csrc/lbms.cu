@@ -251,6 +251,33 @@ cudaError_t build_graph(lbms_t* h, int parity)
 
 }  // namespace
 
+namespace lbms {
+
+int mass_fixed_shift(uint32_t cells) { return fixed_shift_for(cells); }
+
+cudaError_t launch_mass_reduce(int dtype, const void* partials, uint32_t blocks, int n, int shift,
+                               double* out, cudaStream_t stream)
+{
+    if (dtype == LBMS_F32)
+        k_mass_finalize_fixed<<<n, kBlock, 0, stream>>>(static_cast<const long long*>(partials), blocks,
+                                                          n, shift, out);
+    else
+        k_mass_finalize_pairs<<<n, kBlock, 0, stream>>>(static_cast<const double2*>(partials), blocks, n,
+                                                          out);
+    return cudaGetLastError();
+}
+
+int set_call_error(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_error, sizeof(g_create_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+}  // namespace lbms
+
 extern "C" {
 
 size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dtype)

@@ -52,4 +52,13 @@ cudaError_t dispatch_d3q7(Op op, int dtype, const KArgs& a);
 // Number of blocks a node kernel over `cells` nodes is launched with.
 inline uint32_t node_blocks(uint32_t cells) { return (cells + kBlock - 1) / kBlock; }
 
+// Helpers of the host runtime shared with lbms_mass_noalloc (mass_noalloc.cu):
+// fraction bits of the FP32 fixed-point mass partials for a grid, the final
+// reduction of per-block partials into n doubles, and the thread's message for
+// lbms_last_error(NULL).
+int mass_fixed_shift(uint32_t cells);
+cudaError_t launch_mass_reduce(int dtype, const void* partials, uint32_t blocks, int n, int shift,
+                               double* out, cudaStream_t stream);
+int set_call_error(int code, const char* fmt, ...);
+
 }  // namespace lbms

@@ -37,7 +37,8 @@ ERRORS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ERANGE", 6:
 
 EXPORTED = (
     "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_step", "lbms_moments",
-    "lbms_mass", "lbms_status", "lbms_steps_done", "lbms_last_error", "lbms_destroy",
+    "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_last_error",
+    "lbms_destroy",
 )
 
 _lock = threading.Lock()
@@ -80,6 +81,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_moments.restype = I
         L.lbms_mass.argtypes = [P, P]
         L.lbms_mass.restype = I
+        L.lbms_mass_noalloc.argtypes = [I, I, P, I, P, P, P]
+        L.lbms_mass_noalloc.restype = I
         L.lbms_status.argtypes = [P, P]
         L.lbms_status.restype = I
         L.lbms_steps_done.argtypes = [P]
@@ -147,6 +150,17 @@ def lbms_mass(h, n_species: int) -> np.ndarray:
     out = np.zeros(n_species, dtype=np.float64)
     _check(h, load().lbms_mass(h, out.ctypes.data_as(ctypes.c_void_p)), "lbms_mass")
     return out
+
+
+def lbms_mass_noalloc(lattice: int, n_species: int, grid, dtype: int, populations_ptr: int,
+                      mass_out_ptr: int, stream_ptr: int) -> None:
+    """Species totals of a population buffer without a handle or any device
+    allocation (for callers that cannot allocate; see include/lbms.h)."""
+    L = load()
+    rc = L.lbms_mass_noalloc(lattice, n_species, _grid(grid), dtype, ctypes.c_void_p(populations_ptr),
+                             ctypes.c_void_p(mass_out_ptr), ctypes.c_void_p(stream_ptr))
+    if rc != LBMS_OK:
+        raise LbmsError("lbms_mass_noalloc: %s (%s)" % (ERRORS.get(rc, rc), L.lbms_last_error(None).decode()))
 
 
 def lbms_status(h) -> int:
@@ -243,6 +257,17 @@ class Solver:
 
     def mass(self) -> np.ndarray:
         return lbms_mass(self._h, self.n)
+
+    def populations(self) -> torch.Tensor:
+        """View of the current population buffer, shape [n - 1, Q, cells]."""
+        q = Q_OF[self.lattice]
+        es = 8 if self.dtype == torch.float64 else 4
+        nx, ny, nz = self.grid
+        cells = nx * ny * nz
+        nbytes = (self.n - 1) * q * cells * es
+        stride = (nbytes + 255) // 256 * 256
+        off = (self.steps_done % 2) * stride
+        return self.workspace[off:off + nbytes].view(self.dtype).view(self.n - 1, q, cells)
 
     def status(self) -> int:
         return lbms_status(self._h)
