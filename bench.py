@@ -1,22 +1,25 @@
 """Throughput of the fused Maxwell-Stefan MRT stream-collide on GB300.
 
-Workload (default): ternary two-bulb (Loschmidt-like) diffusion on D3Q7, 256^3
-nodes, FP32, no-flux bounce-back walls on all six faces, left half
-x = (0, 0.5, 0.5), right half x = (0.5, 0.5, 0) joined by a tanh interface of
-width 4 cells, D12 : D13 : D23 = 5 : 4 : 1 scaled to max lattice D = 0.1.
+Default workload (--workload tube): ternary two-bulb (Loschmidt-like)
+diffusion on D3Q7, 256^3 nodes, FP32, no-flux bounce-back walls on all six
+faces, left half x = (0, 0.5, 0.5), right half x = (0.5, 0.5, 0) joined by a
+tanh interface of width 4 cells, D12 : D13 : D23 = 5 : 4 : 1 scaled to max
+lattice D = 0.1.  Other workloads (for measurement of the other
+configurations): --workload blobs (D2Q9, 2048^2, 5 species, FP32, periodic,
+seeded Gaussian blobs, D_ij uniform in [0.01, 0.12]) and --workload sine
+(D2Q5, 128^2, ternary, FP64, periodic, seeded sine modes).
 
 One bench step is one lattice Boltzmann time step of the whole grid: pull
-streaming with bounce-back, mole fractions, the per-node Maxwell-Stefan
-relaxation matrices, collision and store (the last step of the timed run also
-writes the FP64 per-species mass partials and reduces them).  The state is
-2 x 940 MB, far larger than the 129 MB L2, so no flush is needed between steps.
+streaming with the boundary faces, mole fractions, the per-node
+Maxwell-Stefan relaxation matrices, collision and store (the last step of
+the timed run also writes the per-species mass partials and reduces them).
 
 Metric: GLUPS = evolved-species node updates per second, S * cells * steps / s
-with S = n - 1 = 2 distributions per node (the n-th species follows from the
+with S = n - 1 distributions per node (the n-th species follows from the
 closure); the n-counted figure is reported beside it.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-slab of the same workload.
+sample of the same workload.
 """
 
 from __future__ import annotations
@@ -30,22 +33,88 @@ import subprocess
 import sys
 import threading
 import time
+from dataclasses import dataclass
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-NX = NY = NZ = 256  # --grid changes these (profiling of smaller copies)
-N_SPECIES = 3
-S_EVOLVED = N_SPECIES - 1
-Q = 7
-D_PAIRS = {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02}
 METRIC = "GLUPS (species-node updates/s) and % of HBM roofline"
-WORKLOAD = ("D3Q7 256^3 ternary two-bulb closed tube, FP32, D12:D13:D23=5:4:1 "
-            "(max lattice D 0.1), no-flux walls")
 KERNEL_SOURCES = ["paper_1808_06787_gb300/csrc/kernels.cuh",
                   "paper_1808_06787_gb300/csrc/node.cuh",
                   "paper_1808_06787_gb300/csrc/lattice.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_d3q7_256cube_f32.json")
+
+
+@dataclass
+class Workload:
+    key: str
+    lattice: str
+    Q: int
+    grid: tuple
+    n: int
+    f64: bool
+    bc: tuple
+    description: str
+    traffic_file: str
+
+    @property
+    def S(self):
+        return self.n - 1
+
+    @property
+    def cells(self):
+        return self.grid[0] * self.grid[1] * self.grid[2]
+
+    @property
+    def es(self):
+        return 8 if self.f64 else 4
+
+    def D(self):
+        import synthetic as sy
+
+        if self.key == "blobs":
+            return sy.random_D(self.n, seed=1003)
+        return sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
+
+    def x0(self, grid=None):
+        import synthetic as sy
+
+        nx, ny, nz = grid or self.grid
+        if self.key == "tube":
+            return sy.two_bulb(nx, ny, nz, width=4.0)
+        if self.key == "blobs":
+            return sy.gaussian_blobs(self.n, nx, ny, seed=1003)
+        return sy.sin_modes(3, nx, ny, amp=0.05, seed=1001)
+
+    def sample_grid(self, cells_target: int):
+        """A block of the workload with about cells_target nodes (oracle timing)."""
+        nx, ny, nz = self.grid
+        if self.key == "tube":  # x-slab of the closed tube: same physics per node
+            sy_ = max(1, min(ny, cells_target // nx))
+            sz = max(1, min(nz, cells_target // (nx * sy_)))
+            return (nx, sy_, sz)
+        side = int(max(8, min(nx, cells_target ** 0.5)))
+        return (side, side, 1)
+
+
+def make_workload(key: str, grid_edge: int) -> Workload:
+    P, W = "periodic", "noflux"
+    if key == "tube":
+        g = (grid_edge, grid_edge, grid_edge)
+        return Workload("tube", "D3Q7", 7, g, 3, False, (W,) * 6,
+                        "D3Q7 %d^3 ternary two-bulb closed tube, FP32, D12:D13:D23=5:4:1 "
+                        "(max lattice D 0.1), no-flux walls" % grid_edge,
+                        "traffic_d3q7_256cube_f32.json")
+    if key == "blobs":
+        e = grid_edge if grid_edge != 256 else 2048
+        return Workload("blobs", "D2Q9", 9, (e, e, 1), 5, False, (P,) * 6,
+                        "D2Q9 %d^2 five species, FP32, periodic, seeded Gaussian blobs "
+                        "(sigma 32, amplitude 0.2), D_ij uniform in [0.01, 0.12]" % e,
+                        "traffic_d2q9_2048sq_n5_f32.json")
+    e = grid_edge if grid_edge != 256 else 128
+    return Workload("sine", "D2Q5", 5, (e, e, 1), 3, True, (P,) * 6,
+                    "D2Q5 %d^2 ternary, FP64, periodic, seeded sine modes, "
+                    "D = (0.10, 0.08, 0.02)" % e,
+                    "traffic_d2q5_128sq_f64.json")
 
 
 def kernel_hash() -> str:
@@ -56,15 +125,15 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
+def measured_traffic(wl: Workload):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     or None when the kernel sources changed since it was taken."""
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(os.path.join(ROOT, "profiles", wl.traffic_file)) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_hash") != kernel_hash():
+    if rec.get("kernel_hash") != kernel_hash() or tuple(rec.get("grid", ())) != tuple(wl.grid):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -133,19 +202,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def initial_field(np):
-    import synthetic as sy
-
-    return sy.two_bulb(NX, NY, NZ, width=4.0)
-
-
-def diffusivities():
-    import synthetic as sy
-
-    return sy.D_from_pairs(N_SPECIES, D_PAIRS)
-
-
-def run_ours(args):
+def run_ours(args, wl: Workload):
     import numpy as np
     import torch
 
@@ -166,14 +223,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    D = diffusivities()
-    x0_host = torch.from_numpy(initial_field(np)).float().pin_memory()
-    cells = NX * NY * NZ
+    tdtype = torch.float64 if wl.f64 else torch.float32
+    x0_host = torch.from_numpy(wl.x0()).to(tdtype).pin_memory()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        s = Solver("D3Q7", D, (NX, NY, NZ), bc="noflux", dtype=torch.float32, stream=stream)
-        x0_dev = x0_host.cuda(non_blocking=True)
-        s.set_state(x0_dev)
+        s = Solver(wl.lattice, wl.D(), wl.grid, bc=wl.bc, dtype=tdtype, stream=stream)
+        s.set_state(x0_host.cuda(non_blocking=True))
         mass0 = s.mass()
         s.step(args.warmup)
         torch.cuda.synchronize()
@@ -196,15 +251,15 @@ def run_ours(args):
 
         # end to end through the public API with host buffers: pinned x0 in,
         # K steps, mole fractions and masses back to pinned host memory
-        x_host = torch.empty(s.field_shape, dtype=torch.float32).pin_memory()
-        e2e_s, mass_e2e = None, None
+        x_host = torch.empty(s.field_shape, dtype=tdtype).pin_memory()
+        e2e_s = None
         if not args.no_e2e:
             barrier()
             t0 = time.perf_counter()
             s.set_state(x0_host)
             s.step(args.steps)
             s.moments(x_host)
-            mass_e2e = s.mass()
+            s.mass()
             barrier()
             e2e_s = time.perf_counter() - t0
 
@@ -218,13 +273,13 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    updates = float(S_EVOLVED) * cells * args.steps * world
+    cells = wl.cells
+    updates = float(wl.S) * cells * args.steps * world
     glups = updates / (t_ms * 1e-3) / 1e9
-    bytes_per_launch = 2.0 * S_EVOLVED * Q * 4 * cells
-    launch_s = t_ms * 1e-3 / args.steps
-    achieved = bytes_per_launch / launch_s / 1e9
+    bytes_per_launch = 2.0 * wl.S * wl.Q * wl.es * cells
+    achieved = bytes_per_launch / (t_ms * 1e-3 / args.steps) / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = measured_traffic()
+    state_gb = bytes_per_launch / 1e9
     out = {
         "metric": METRIC,
         "value": round(glups, 4),
@@ -236,15 +291,19 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic (seeded two-bulb tanh profile; no dataset)",
+        "dtype": "f64" if wl.f64 else "f32",
+        "data": "synthetic (seeded %s; no dataset)" % {"tube": "two-bulb tanh profile",
+                                                      "blobs": "Gaussian blobs",
+                                                      "sine": "sine modes"}[wl.key],
         "config": {
-            "workload": WORKLOAD if NX == 256 else WORKLOAD.replace("256^3", "%d^3" % NX),
-            "lattice": "D3Q7", "grid": [NX, NY, NZ], "n_species": N_SPECIES,
-            "evolved_species": S_EVOLVED, "bc": "no-flux all faces",
+            "workload": wl.description,
+            "lattice": wl.lattice, "grid": list(wl.grid), "n_species": wl.n,
+            "evolved_species": wl.S, "bc": "no-flux all faces" if wl.key == "tube" else "periodic",
             "relax": "MRT, Lambda_2 by Eq. 3-16",
-            "glups_n_counted": round(glups * N_SPECIES / S_EVOLVED, 4),
-            "l2": "state %.2f GB per step vs 129 MB L2; no flush" % (2 * S_EVOLVED * Q * 4 * NX * NY * NZ / 1e9),
+            "glups_n_counted": round(glups * wl.n / wl.S, 4),
+            "l2": ("state %.2f GB per step vs 129 MB L2; no flush" % state_gb) if state_gb > 0.5
+            else ("state %.1f MB per step is L2-resident: L2/latency bound, not an HBM test"
+                  % (state_gb * 1e3)),
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
         "roofline": {
@@ -253,15 +312,15 @@ def run_ours(args):
             "peak": peak,
             "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": traffic,
+            "traffic": measured_traffic(wl),
             "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": bytes_per_launch,
         },
         "e2e": None if args.no_e2e else {
             "value": round(updates / (e2e_ms * 1e-3) / 1e9, 4),
             "unit": "GLUPS",
-            "h2d_bytes_per_step": round(x0_host.numel() * 4 / args.steps, 1),
-            "d2h_bytes_per_step": round((x_host.numel() * 4 + 8 * N_SPECIES) / args.steps, 1),
+            "h2d_bytes_per_step": round(x0_host.numel() * wl.es / args.steps, 1),
+            "d2h_bytes_per_step": round((x_host.numel() * wl.es + 8 * wl.n) / args.steps, 1),
         },
         "gpu_launches": args.steps + 1,
         "clocks": clocks,
@@ -269,54 +328,49 @@ def run_ours(args):
         "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
     }
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
 
-def _oracle_sample_run(cells_target: int, steps: int):
-    """Time the oracle on a slab of the workload with about cells_target nodes."""
-    import numpy as np
-
+def _oracle_sample_run(wl: Workload, cells_target: int, steps: int):
+    """Time the oracle on a block of the workload with about cells_target nodes."""
     import oracle
-    import synthetic as sy
 
-    ny = max(1, min(NY, cells_target // NX))
-    nz = max(1, min(NZ, cells_target // (NX * ny)))
-    x0 = sy.two_bulb(NX, ny, nz, width=4.0)
+    g = wl.sample_grid(cells_target)
+    x0 = wl.x0(g)
     t0 = time.perf_counter()
-    oracle.run("D3Q7", diffusivities(), x0, steps, bc=("noflux",) * 6)
-    dt = time.perf_counter() - t0
-    return dt, (NX, ny, nz)
+    oracle.run(wl.lattice, wl.D(), x0, steps, bc=wl.bc)
+    return time.perf_counter() - t0, g
 
 
-def cpu_baseline(budget_s: float = 20.0):
+def cpu_baseline(wl: Workload, budget_s: float = 20.0):
     """The oracle as it stands, timed on the host cores over a bounded sample."""
     import oracle
 
     oracle.build()
-    dt1, _ = _oracle_sample_run(NX * NY, 1)
-    rate = NX * NY / dt1  # node updates per second
-    cells_full = NX * NY * NZ
-    if rate * budget_s >= cells_full:
-        cells = cells_full
-        steps = int(max(1, min(50, rate * budget_s / cells_full)))
+    probe = min(wl.cells, 65536)
+    dt1, g1 = _oracle_sample_run(wl, probe, 1)
+    rate = g1[0] * g1[1] * g1[2] / dt1  # node updates per second
+    if rate * budget_s >= wl.cells:
+        cells = wl.cells
+        steps = int(max(1, min(200, rate * budget_s / wl.cells)))
     else:
-        cells, steps = int(max(NX, rate * budget_s)), 1
-    dt, shape = _oracle_sample_run(cells, steps)
-    n = shape[0] * shape[1] * shape[2]
+        cells, steps = int(max(64, rate * budget_s)), 1
+    dt, g = _oracle_sample_run(wl, cells, steps)
+    n = g[0] * g[1] * g[2]
     return {
-        "value": round(S_EVOLVED * n * steps / dt / 1e9, 6),
+        "value": round(wl.S * n * steps / dt / 1e9, 6),
         "unit": "GLUPS",
         "cores": oracle.get_threads(),
         "kind": "oracle",
-        "sample": "%d step(s) on a %dx%dx%d block of the closed tube (FP64 oracle, OpenMP), %.1f s"
-                  % (steps, shape[0], shape[1], shape[2], dt),
+        "sample": "%d step(s) on a %dx%dx%d block of the workload (FP64 oracle, OpenMP), %.1f s"
+                  % (steps, g[0], g[1], g[2], dt),
     }
 
 
-def run_reference(args):
+def run_reference(args, wl: Workload):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -324,15 +378,17 @@ def run_reference(args):
 
     oracle.build()
     budget = args.cpu_budget * 4
-    dt, _ = _oracle_sample_run(NX * 16, 1)
-    rate = NX * 16 / dt
-    cells = int(max(NX, min(NX * NY * NZ, rate * budget / max(1, args.steps + args.warmup))))
-    _oracle_sample_run(cells, args.warmup) if args.warmup else None
-    dt, shape = _oracle_sample_run(cells, args.steps)
-    n = shape[0] * shape[1] * shape[2]
-    glups = S_EVOLVED * n * args.steps / dt / 1e9
-    sample = ("%d timed steps (after %d warm-up) on a %dx%dx%d slab of the closed tube, FP64 "
-              "oracle, %.1f s" % (args.steps, args.warmup, shape[0], shape[1], shape[2], dt))
+    probe = min(wl.cells, 4096)
+    dt1, g1 = _oracle_sample_run(wl, probe, 1)
+    rate = g1[0] * g1[1] * g1[2] / dt1
+    cells = int(max(64, min(wl.cells, rate * budget / max(1, args.steps + args.warmup))))
+    if args.warmup:
+        _oracle_sample_run(wl, cells, args.warmup)
+    dt, g = _oracle_sample_run(wl, cells, args.steps)
+    n = g[0] * g[1] * g[2]
+    glups = wl.S * n * args.steps / dt / 1e9
+    sample = ("%d timed steps (after %d warm-up) on a %dx%dx%d block of the workload, FP64 "
+              "oracle, %.1f s" % (args.steps, args.warmup, g[0], g[1], g[2], dt))
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -346,9 +402,9 @@ def run_reference(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded two-bulb tanh profile; no dataset)",
-        "config": {"workload": WORKLOAD, "lattice": "D3Q7", "grid": [NX, NY, NZ],
-                   "n_species": N_SPECIES},
+        "data": "synthetic (same generator as the GPU arm; no dataset)",
+        "config": {"workload": wl.description, "lattice": wl.lattice, "grid": list(wl.grid),
+                   "n_species": wl.n},
         "cpu_baseline": {"value": round(glups, 6), "unit": "GLUPS", "cores": oracle.get_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(glups, 6), "unit": "GLUPS", "h2d_bytes_per_step": 0,
@@ -363,21 +419,21 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["tube", "blobs", "sine"], default="tube")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--grid", type=int, default=256,
-                    help="edge of the cubic grid (256 is the benchmarked workload)")
+                    help="grid edge (256 selects each workload's own size)")
     args = ap.parse_args()
-    global NX, NY, NZ
-    NX = NY = NZ = args.grid
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    wl = make_workload(args.workload, args.grid)
     if args.impl == "reference":
-        run_reference(args)
+        run_reference(args, wl)
     else:
-        run_ours(args)
+        run_ours(args, wl)
 
 
 if __name__ == "__main__":
