@@ -205,6 +205,95 @@ const char* lbms_last_error(const lbms_t* h);
 /* Release the handle.  Does not free the caller's workspace. */
 void lbms_destroy(lbms_t* h);
 
+/* ========================================================================= */
+/* Batched solves: many independent problems of one lattice, species count   */
+/* and dtype, each with its own grid, diffusivities and faces, stepped        */
+/* together (the model of Sec. 3.1 applied to every instance).                */
+/* ========================================================================= */
+
+typedef struct lbms_batch_s lbms_batch_t;
+
+/* Number of step schedules lbms_batch_tune chooses from. */
+#define LBMS_BATCH_CANDIDATES 7
+
+/*
+ * Workspace bytes for `count` instances with grids[3 * i + {0,1,2}] = {nx, ny,
+ * nz} of instance i (0 for an invalid combination).  Instance i owns
+ * ceil(cells_i / 256) * 256 node slots of one shared node space; the
+ * workspace holds two population buffers over that space, per-block mass
+ * partials, the instance tables and a staging area for host I/O (at least the
+ * largest instance's fields, at least 16 MiB).
+ */
+size_t lbms_batch_workspace_size(int lattice, int n_species, int count, const int* grids, int dtype);
+
+/*
+ * Create a batch.  lattice, n_species, relax, dtype, workspace and cuda_stream
+ * as for lbms_create; the total node slots must stay below LBMS_MAX_CELLS.
+ *   grids  host array of count * 3 extents.
+ *   D      host array of count * n * n diffusivities (instance-major), each
+ *          block symmetric with positive off-diagonal entries.
+ *   bc     host array of count * 6 face kinds as for lbms_create, or NULL for
+ *          all periodic.
+ * Errors as for lbms_create (messages via lbms_batch_last_error(NULL)).
+ */
+int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count, const int* grids,
+                      const double* D, int relax, const int* bc, int dtype, void* workspace,
+                      size_t workspace_bytes, void* cuda_stream);
+
+/*
+ * Initialise every instance from mole fractions (Sec. 4 initialisation, as
+ * lbms_set_state).  Instance i's field is [n][nz][ny][nx] at element offset
+ * offsets[i] of x0; offsets == NULL means packed (instance after instance).
+ * x0 may be host or device memory; a host x0 synchronises the stream.
+ */
+int lbms_batch_set_state(lbms_batch_t* b, const void* x0, const int64_t* offsets);
+
+/*
+ * Advance every instance by n_steps (Eqs. 3-13a/3-13b), with the schedule
+ * chosen by lbms_batch_tune or lbms_batch_set_schedule (default: 0, all
+ * instances per launch).  Each instance evolves exactly as lbms_step would
+ * evolve it alone, bit for bit.  The last step writes the mass partials.
+ */
+int lbms_batch_step(lbms_batch_t* b, long n_steps);
+
+/*
+ * Mole fractions (and fluxes if J_sigma != NULL) of every instance, as
+ * lbms_moments: instance i's x block at element offsets[i] of x_sigma and its
+ * J block ([n][dim][cells]) at element dim * offsets[i] of J_sigma; offsets ==
+ * NULL means packed.  Host or device buffers; synchronises the stream.
+ */
+int lbms_batch_moments(lbms_batch_t* b, void* x_sigma, void* J_sigma, const int64_t* offsets);
+
+/* Per-instance species totals, mass_out[i * n + s], as lbms_mass.  Host array;
+ * synchronises the stream. */
+int lbms_batch_mass(lbms_batch_t* b, double* mass_out);
+
+/* OR of the status flags of all instances.  Synchronises the stream. */
+int lbms_batch_status(lbms_batch_t* b, uint32_t* flags);
+
+/*
+ * Step schedules: 0 streams all instances through HBM every step (CUDA graph
+ * of 32 steps); 1..6 run groups of consecutive instances whose two population
+ * buffers fit in 24, 24, 48, 48, 96, 96 MB for 8 or 32 steps each (chunk
+ * 8, 32, 8, 32, 8, 32), so that a group stays in L2 between its steps.
+ * Results do not depend on the schedule.
+ */
+int lbms_batch_set_schedule(lbms_batch_t* b, int candidate);
+int lbms_batch_get_schedule(const lbms_batch_t* b);
+
+/*
+ * Schedule tuner: times every candidate over trial_steps steps (after one
+ * untimed warm-up of the same length), keeps the fastest and returns it in
+ * *chosen; ms_per_step, if not NULL, receives LBMS_BATCH_CANDIDATES timings.
+ * It advances the instances by 2 * LBMS_BATCH_CANDIDATES * trial_steps steps:
+ * call it before lbms_batch_set_state.
+ */
+int lbms_batch_tune(lbms_batch_t* b, int trial_steps, double* ms_per_step, int* chosen);
+
+long lbms_batch_steps_done(const lbms_batch_t* b);
+const char* lbms_batch_last_error(const lbms_batch_t* b);
+void lbms_batch_destroy(lbms_batch_t* b);
+
 #ifdef __cplusplus
 }
 #endif

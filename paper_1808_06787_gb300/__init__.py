@@ -8,6 +8,7 @@ PyTorch only for device memory and streams.
 
 from .lbms import (  # noqa: F401
     EXPORTED,
+    BatchSolver,
     LbmsError,
     Solver,
     lbms_create,

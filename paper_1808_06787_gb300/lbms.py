@@ -39,7 +39,12 @@ EXPORTED = (
     "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_step", "lbms_moments",
     "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_last_error",
     "lbms_destroy",
+    "lbms_batch_workspace_size", "lbms_batch_create", "lbms_batch_set_state", "lbms_batch_step",
+    "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_schedule",
+    "lbms_batch_get_schedule", "lbms_batch_tune", "lbms_batch_steps_done",
+    "lbms_batch_last_error", "lbms_batch_destroy",
 )
+BATCH_CANDIDATES = 7
 
 _lock = threading.Lock()
 _lib = None
@@ -91,6 +96,32 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_last_error.restype = ctypes.c_char_p
         L.lbms_destroy.argtypes = [P]
         L.lbms_destroy.restype = None
+        L.lbms_batch_workspace_size.argtypes = [I, I, I, P, I]
+        L.lbms_batch_workspace_size.restype = SZ
+        L.lbms_batch_create.argtypes = [P, I, I, I, P, P, I, P, I, P, SZ, P]
+        L.lbms_batch_create.restype = I
+        L.lbms_batch_set_state.argtypes = [P, P, P]
+        L.lbms_batch_set_state.restype = I
+        L.lbms_batch_step.argtypes = [P, ctypes.c_long]
+        L.lbms_batch_step.restype = I
+        L.lbms_batch_moments.argtypes = [P, P, P, P]
+        L.lbms_batch_moments.restype = I
+        L.lbms_batch_mass.argtypes = [P, P]
+        L.lbms_batch_mass.restype = I
+        L.lbms_batch_status.argtypes = [P, P]
+        L.lbms_batch_status.restype = I
+        L.lbms_batch_set_schedule.argtypes = [P, I]
+        L.lbms_batch_set_schedule.restype = I
+        L.lbms_batch_get_schedule.argtypes = [P]
+        L.lbms_batch_get_schedule.restype = I
+        L.lbms_batch_tune.argtypes = [P, I, P, P]
+        L.lbms_batch_tune.restype = I
+        L.lbms_batch_steps_done.argtypes = [P]
+        L.lbms_batch_steps_done.restype = ctypes.c_long
+        L.lbms_batch_last_error.argtypes = [P]
+        L.lbms_batch_last_error.restype = ctypes.c_char_p
+        L.lbms_batch_destroy.argtypes = [P]
+        L.lbms_batch_destroy.restype = None
         _lib = L
         return L
 
@@ -279,6 +310,150 @@ class Solver:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lbms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- batched solves --------------------------------------------------------
+
+def _bcheck(b, rc: int, what: str) -> None:
+    if rc != LBMS_OK:
+        raise LbmsError("%s: %s (%s)" % (what, ERRORS.get(rc, rc),
+                                         load().lbms_batch_last_error(b).decode()))
+
+
+def lbms_batch_workspace_size(lattice: int, n_species: int, grids, dtype: int) -> int:
+    g = np.ascontiguousarray(np.asarray(grids, dtype=np.int32).reshape(-1, 3))
+    return int(load().lbms_batch_workspace_size(lattice, n_species, g.shape[0],
+                                                g.ctypes.data_as(ctypes.c_void_p), dtype))
+
+
+class BatchSolver:
+    """Many independent solves of one lattice / species count / dtype.
+
+    ``grids``: list of (nx, ny[, nz]); ``Ds``: list (or array) of n x n
+    diffusivity matrices; ``bcs``: None (all periodic) or a list of 6-tuples of
+    face kinds.  Fields are exchanged as lists of [n, nz, ny, nx] tensors or as
+    one packed 1-D tensor (instance after instance).
+    """
+
+    def __init__(self, lattice: str, Ds, grids, *, bcs=None, relax: str = "magic",
+                 dtype=torch.float32, device="cuda", stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise LbmsError("the lbms solver needs a CUDA device")
+        L = load()
+        self.lattice = lattice
+        self.dim = DIMS[lattice]
+        self.dtype = dtype
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.grids = [tuple(int(v) for v in (list(g) + [1] * (3 - len(g)))) for g in grids]
+        self.count = len(self.grids)
+        D = np.ascontiguousarray(np.asarray(Ds, dtype=np.float64).reshape(self.count, -1))
+        self.n = int(round(D.shape[1] ** 0.5))
+        self.cells = [g[0] * g[1] * g[2] for g in self.grids]
+        self.offsets = np.zeros(self.count + 1, dtype=np.int64)
+        self.offsets[1:] = np.cumsum([self.n * c for c in self.cells])
+        g = np.ascontiguousarray(np.asarray(self.grids, dtype=np.int32))
+        self._g = g
+        dt = DTYPES[dtype]
+        nbytes = int(L.lbms_batch_workspace_size(LATTICES[lattice], self.n, self.count,
+                                                 g.ctypes.data_as(ctypes.c_void_p), dt))
+        if nbytes == 0:
+            raise LbmsError("invalid batch (lattice/species/grids/dtype)")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        bc = None
+        if bcs is not None:
+            bc = np.ascontiguousarray(np.array(
+                [[FACE[v] if isinstance(v, str) else int(v) for v in (b if not isinstance(b, str) else (b,) * 6)]
+                 for b in bcs], dtype=np.int32))
+        self._h = ctypes.c_void_p()
+        rc = L.lbms_batch_create(ctypes.byref(self._h), LATTICES[lattice], self.n, self.count,
+                                 g.ctypes.data_as(ctypes.c_void_p), D.ctypes.data_as(ctypes.c_void_p),
+                                 RELAX[relax], bc.ctypes.data_as(ctypes.c_void_p) if bc is not None else None,
+                                 dt, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != LBMS_OK:
+            self._h = None
+            raise LbmsError("lbms_batch_create: %s (%s)" % (ERRORS.get(rc, rc),
+                                                            L.lbms_batch_last_error(None).decode()))
+
+    def pack(self, fields) -> torch.Tensor:
+        """Concatenate per-instance [n, nz, ny, nx] arrays into one flat tensor."""
+        parts = [torch.as_tensor(np.ascontiguousarray(f) if isinstance(f, np.ndarray) else f)
+                 .reshape(-1).to(self.dtype) for f in fields]
+        return torch.cat(parts)
+
+    def unpack(self, flat: torch.Tensor, per=1):
+        out = []
+        for i, (nx, ny, nz) in enumerate(self.grids):
+            a, b = int(self.offsets[i]) * per, int(self.offsets[i + 1]) * per
+            shape = (self.n, self.dim, nz, ny, nx) if per > 1 else (self.n, nz, ny, nx)
+            out.append(flat[a:b].view(shape))
+        return out
+
+    def set_state(self, x0) -> None:
+        flat = x0 if isinstance(x0, torch.Tensor) and x0.dim() == 1 else self.pack(x0)
+        if flat.numel() != int(self.offsets[-1]) or flat.dtype != self.dtype:
+            raise ValueError("packed field has the wrong size or dtype")
+        flat = flat.contiguous()
+        _bcheck(self._h, load().lbms_batch_set_state(self._h, ctypes.c_void_p(flat.data_ptr()), None),
+                "lbms_batch_set_state")
+        self._keep = flat
+
+    def step(self, n: int) -> None:
+        _bcheck(self._h, load().lbms_batch_step(self._h, int(n)), "lbms_batch_step")
+
+    def moments(self, flux: bool = False, out_device=None):
+        dev = self.device if out_device is None else torch.device(out_device)
+        x = torch.empty(int(self.offsets[-1]), dtype=self.dtype, device=dev)
+        J = torch.empty(int(self.offsets[-1]) * self.dim, dtype=self.dtype, device=dev) if flux else None
+        if dev.type == "cpu":
+            x = x.pin_memory()
+            J = J.pin_memory() if J is not None else None
+        _bcheck(self._h, load().lbms_batch_moments(self._h, ctypes.c_void_p(x.data_ptr()),
+                                                   ctypes.c_void_p(J.data_ptr()) if J is not None else None,
+                                                   None), "lbms_batch_moments")
+        return (x, J) if flux else x
+
+    def mass(self) -> np.ndarray:
+        out = np.zeros(self.count * self.n, dtype=np.float64)
+        _bcheck(self._h, load().lbms_batch_mass(self._h, out.ctypes.data_as(ctypes.c_void_p)), "lbms_batch_mass")
+        return out.reshape(self.count, self.n)
+
+    def status(self) -> int:
+        fl = ctypes.c_uint32()
+        _bcheck(self._h, load().lbms_batch_status(self._h, ctypes.byref(fl)), "lbms_batch_status")
+        return int(fl.value)
+
+    def set_schedule(self, candidate: int) -> None:
+        _bcheck(self._h, load().lbms_batch_set_schedule(self._h, int(candidate)), "lbms_batch_set_schedule")
+
+    @property
+    def schedule(self) -> int:
+        return int(load().lbms_batch_get_schedule(self._h))
+
+    def tune(self, trial_steps: int = 32):
+        """Time every step schedule and keep the fastest (advances the state: call
+        before set_state).  Returns (chosen, ms_per_step of each candidate)."""
+        times = np.zeros(BATCH_CANDIDATES, dtype=np.float64)
+        chosen = ctypes.c_int()
+        _bcheck(self._h, load().lbms_batch_tune(self._h, int(trial_steps), times.ctypes.data_as(ctypes.c_void_p),
+                                                ctypes.byref(chosen)), "lbms_batch_tune")
+        return int(chosen.value), times
+
+    @property
+    def steps_done(self) -> int:
+        return int(load().lbms_batch_steps_done(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().lbms_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -38,6 +38,8 @@ __all__ = [
     "duncan_toor_1d",
     "loschmidt_1d",
     "small_mode",
+    "batch_instances",
+    "batch_field",
 ]
 
 
@@ -154,3 +156,32 @@ def small_mode(xbar, vec, eps: float, nx: int, ny: int = 1, nz: int = 1, *,
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     ph = 2.0 * math.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz)
     return xbar[:, None, None, None] + eps * vec[:, None, None, None] * np.cos(ph)[None]
+
+
+def batch_instances(count: int, *, lo: int = 32, hi: int = 256, seed: int = 1004,
+                    d_lo: float = 0.01, d_hi: float = 0.12):
+    """Uneven ternary D2Q5 instances: square side L uniform in [lo, hi], seeded
+    diffusivities uniform in [d_lo, d_hi]; even instances get one sine mode per
+    species on a periodic grid, odd instances the two-bulb tanh profile along x
+    with no-flux x faces and periodic y.
+
+    Returns (grids[count, 3], D[count, 3, 3], bcs: list of count 6-tuples); the
+    initial fields come one at a time from ``batch_field(i, L_i)``.
+    """
+    g = rng(seed)
+    sides = g.integers(lo, hi + 1, size=count)
+    grids = np.stack([sides, sides, np.ones_like(sides)], axis=1).astype(np.int32)
+    Ds = np.empty((count, 3, 3))
+    for i in range(count):
+        d12, d13, d23 = g.uniform(d_lo, d_hi, size=3)
+        Ds[i] = D_from_pairs(3, {(1, 2): d12, (1, 3): d13, (2, 3): d23})
+    P, W = "periodic", "noflux"
+    bcs = [(P,) * 6 if i % 2 == 0 else (W, W, P, P, P, P) for i in range(count)]
+    return grids, Ds, bcs
+
+
+def batch_field(i: int, side: int, *, seed: int = 1004) -> np.ndarray:
+    """Initial field of instance i of ``batch_instances`` (see there)."""
+    if i % 2 == 0:
+        return sin_modes(3, side, side, amp=0.05, seed=seed * 7919 + i)
+    return two_bulb(side, side, 1, width=4.0)
