@@ -195,6 +195,47 @@ int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], int dtype,
 /* OR of the status flags raised since lbms_set_state.  Synchronises the stream. */
 int lbms_status(lbms_t* h, uint32_t* flags);
 
+/*
+ * Checkpoints.  lbms_get_state copies the current post-collision populations,
+ * S * Q * cells elements laid out [s][k][z][y][x] (k in the library's velocity
+ * order: rest, then opposite pairs), to f_out (host or device).
+ * lbms_set_state_raw loads such a buffer and sets the step count to `step`, so
+ * that the following steps reproduce a run that had reached step `step` from
+ * that state bit for bit (the stochastic rounding of FP32 solvers is keyed by
+ * the step count).  Host buffers synchronise the stream.
+ */
+int lbms_get_state(lbms_t* h, void* f_out);
+int lbms_set_state_raw(lbms_t* h, const void* f_in, long step);
+
+/*
+ * Adjoint (reverse-mode derivative) of the step, for gradients of a loss L of
+ * the final mole fractions with respect to the binary diffusivities D_ij and
+ * the initial field.  It differentiates the model's map f+(t-1) -> f+(t)
+ * (propagation Eq. 3-13b, collision Eq. 3-13a with Lambda_1 from Eq. 3-26 and
+ * Lambda_2 from Eq. 3-16, f_eq of Eq. 3-3) in exact arithmetic.  Up to 5
+ * species.  All buffers are device memory of the handle's dtype unless noted;
+ * lambda buffers have the population layout (S * Q * cells).
+ *   lbms_adjoint_scratch_size  bytes of the gradient accumulator gacc
+ *                              (FP64, per block and species pair); zero it
+ *                              before the first step of a backward pass.
+ *   lbms_adjoint_seed     lambda(T) from dL/dxi(T) ([n][cells], all species,
+ *                         the closure species' entry included).
+ *   lbms_adjoint_step     lambda(t-1) from lambda(t) (lam_in != lam_out), given
+ *                         the forward populations f+(t-1) of that step;
+ *                         accumulates dL/d(1/D) into gacc.
+ *   lbms_adjoint_initial  dL/dx0 ([n][cells]) from lambda(0) (f+(0) = w_k x0);
+ *                         the closure species does not enter the model and
+ *                         gets zero.
+ *   lbms_adjoint_reduce   dL/dD_pq for the pairs p < q in the order (0,1),
+ *                         (0,2), .., (0,n-1), (1,2), .. into dL_dD (host or
+ *                         device, n (n-1) / 2 doubles); synchronises the stream.
+ */
+size_t lbms_adjoint_scratch_size(const lbms_t* h);
+int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam);
+int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* lam_out, void* gacc);
+int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0);
+int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD);
+
 /* Number of steps taken since lbms_set_state, or -1 for a NULL handle. */
 long lbms_steps_done(const lbms_t* h);
 

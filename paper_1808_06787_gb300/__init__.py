@@ -23,3 +23,4 @@ from .lbms import (  # noqa: F401
     lbms_workspace_size,
     load,
 )
+from .autograd import MaxwellStefanLB, RunSpec, simulate  # noqa: F401

@@ -1,0 +1,111 @@
+"""Gradients of a loss of the final mole fractions with respect to the binary
+diffusivities and the initial field, through the hand-written adjoint kernels.
+
+``MaxwellStefanLB.apply(x0, d_pairs, spec)`` runs ``spec.steps`` steps of the
+model from the initial mole fractions ``x0`` ([n, nz, ny, nx], on the device,
+the solver's dtype) with the pair diffusivities ``d_pairs`` (1-D float64 CPU
+tensor, pairs (0,1), (0,2), .., (0,n-1), (1,2), ..) and returns the mole
+fractions at the final step.  Its backward pass applies the adjoint step
+kernels from the last step to the first with sqrt(T) checkpointing: the
+forward keeps the populations every K = ceil(sqrt(T)) steps, and the backward
+pass recomputes each segment of K states from its checkpoint (bit for bit:
+the step count keys the stochastic rounding) before stepping the adjoint
+through it, so the extra cost is one forward pass and the memory is about
+2 sqrt(T) population buffers.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .lbms import Solver
+
+
+@dataclass
+class RunSpec:
+    lattice: str
+    grid: tuple
+    steps: int
+    bc: object = "periodic"
+    relax: str = "magic"
+    dtype: torch.dtype = torch.float32
+    stats: dict = field(default_factory=dict)
+
+
+def pairs_to_matrix(d_pairs, n: int) -> np.ndarray:
+    D = np.ones((n, n))
+    k = 0
+    for p in range(n):
+        for q in range(p + 1, n):
+            D[p, q] = D[q, p] = float(d_pairs[k])
+            k += 1
+    return D
+
+
+def n_from_pairs(npairs: int) -> int:
+    n = int(round((1 + math.sqrt(1 + 8 * npairs)) / 2))
+    if n * (n - 1) // 2 != npairs:
+        raise ValueError("d_pairs must hold n (n - 1) / 2 entries")
+    return n
+
+
+class MaxwellStefanLB(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x0: torch.Tensor, d_pairs: torch.Tensor, spec: RunSpec):
+        n = n_from_pairs(d_pairs.numel())
+        D = pairs_to_matrix(d_pairs.detach().cpu().double().numpy(), n)
+        solver = Solver(spec.lattice, D, spec.grid, bc=spec.bc, relax=spec.relax, dtype=spec.dtype,
+                        device=x0.device)
+        solver.set_state(x0.detach().to(spec.dtype).contiguous())
+        T = int(spec.steps)
+        K = max(1, int(math.ceil(math.sqrt(T))))
+        ckpts = []
+        t = 0
+        while t < T:
+            ckpts.append((t, solver.get_state()))
+            m = min(K, T - t)
+            solver.step(m)
+            t += m
+        xT = solver.moments()
+        ctx.solver = solver
+        ctx.x0_dtype = x0.dtype
+        ctx.ckpts = ckpts
+        ctx.K = K
+        ctx.T = T
+        ctx.spec = spec
+        spec.stats["checkpoints"] = len(ckpts)
+        spec.stats["segment"] = K
+        return xT
+
+    @staticmethod
+    def backward(ctx, grad_xT: torch.Tensor):
+        s = ctx.solver
+        lam = torch.empty(s.state_shape, dtype=s.dtype, device=s.device)
+        lam2 = torch.empty_like(lam)
+        s.adjoint_seed(grad_xT.to(s.dtype), lam)
+        gacc = s.adjoint_scratch()
+        seg = [torch.empty(s.state_shape, dtype=s.dtype, device=s.device) for _ in range(ctx.K)]
+        for t0, ck in reversed(ctx.ckpts):
+            t1 = min(t0 + ctx.K, ctx.T)
+            # recompute f+(t0) .. f+(t1 - 1) from the checkpoint
+            seg[0].copy_(ck)
+            s.set_state_raw(ck, t0)
+            for j in range(1, t1 - t0):
+                s.step(1)
+                s.get_state(seg[j])
+            # adjoint steps t1 .. t0 + 1 (step t reads f+(t - 1))
+            for t in range(t1, t0, -1):
+                s.adjoint_step(seg[t - 1 - t0], lam, lam2, gacc)
+                lam, lam2 = lam2, lam
+        grad_x0 = s.adjoint_initial(lam).to(ctx.x0_dtype)
+        gD = torch.from_numpy(s.adjoint_reduce(gacc))
+        return grad_x0, gD, None
+
+
+def simulate(x0: torch.Tensor, d_pairs: torch.Tensor, spec: RunSpec) -> torch.Tensor:
+    """Differentiable final mole fractions (see the module docstring)."""
+    return MaxwellStefanLB.apply(x0, d_pairs, spec)

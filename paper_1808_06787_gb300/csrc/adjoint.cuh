@@ -1,0 +1,381 @@
+// Adjoint (reverse-mode derivative) of the stream-collide step.
+//
+// The forward step maps the stored post-collision populations f+(t-1) to f+(t):
+// a gather f(t) = P f+(t-1) (propagation, Eq. 3-13b, with the faces' bounce-back
+// or wrap), then at every node the collision f+ = f - Omega(xi) (f - W f) of
+// Eq. 3-13a, with W f = w_k xi (Eq. 3-3) and Omega = Lambda_1 on the odd and
+// Lambda_2 on the even part of every opposite pair (Sec. 3.1), Lambda_1 from
+// Eq. 3-26 and Lambda_2 from Eq. 3-16.  Its adjoint takes lambda(t) = dL/df+(t)
+// to lambda(t-1) = dL/df+(t-1):
+//   mu = lambda - (I - W)^T Omega^T lambda                      (Lambda fixed)
+//        + s_m on every population of species m                  (through Lambda(xi))
+//   lambda(t-1) = P^T mu   (P is a permutation: each mu(x, k) goes back to the
+//                           slot the gather read it from)
+// with, for m < n-1 (the closure xi_n = 1 - sum xi enters B):
+//   s_m = - sum_ab E_m[a][b] Z[a][b],  E_m = dB/dxi_m,
+//   Z   = K^{-T} H (I - Lambda_1/2)^T,  K = I/c_s^2 + B/2,
+//   H_ij = <lambda^i, odd(g^j)> + <lambda^i, even(g^j)> r_ij,  g = f - W f,
+//   r_ii = dlambda_2/dlambda_1 = -48 / (lambda_1 - 8)^2 (Eq. 3-16), r_ij = 1 else,
+// because dLambda_1 = K^{-1} dB (I - Lambda_1/2).  The same Z gives the
+// derivative with respect to c_pq = 1/D_pq: dL/dc_pq += - sum_ab F_pq[a][b]
+// Z[a][b] with F_pq = dB/dc_pq (Eq. 2-10).  The derivative is that of the
+// exact-arithmetic map (the forward's rest-population bookkeeping and rounding
+// are exact reformulations and rounding, not part of the model).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace lbms {
+
+template <int S>
+struct NPairs {
+    static constexpr int value = (S + 1) * S / 2;  // pairs {p, q} of the n = S + 1 species
+};
+
+// Pair index of {p, q}, p < q <= S, in the order (0,1), (0,2), .., (0,S), (1,2), ..
+__host__ __device__ constexpr int pair_index(int p, int q, int S)
+{
+    return p * (2 * (S + 1) - p - 1) / 2 + (q - p - 1);
+}
+
+template <int LAT, int S, typename T, typename InvD>
+__device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
+                                             const T (&lam)[S][Lattice<LAT>::Q], const InvD& invD,
+                                             T cs2inv, int relax, T (&mu)[S][Lattice<LAT>::Q],
+                                             T (&dc)[NPairs<S>::value])
+{
+    using L = Lattice<LAT>;
+    constexpr int Q = L::Q;
+    T xi[S + 1];
+    mole_fractions<LAT, S, T>(f, xi);
+    // B (Eq. 2-10), K, and Gauss-Jordan on [K | B | I] -> Lambda_1 = K^{-1} B, K^{-1}
+    T K[S][S], L1[S][S], Ki[S][S];
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            T b;
+            if (i != j) {
+                b = xi[i] * (invD[i][S] - invD[i][j]);
+            } else {
+                b = xi[i] * invD[i][S];
+#pragma unroll
+                for (int k = 0; k <= S; ++k)
+                    if (k != i) b += xi[k] * invD[i][k];
+            }
+            L1[i][j] = b;
+            K[i][j] = T(0.5) * b + (i == j ? cs2inv : T(0));
+            Ki[i][j] = i == j ? T(1) : T(0);
+        }
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+        const T inv = recip(K[p][p]);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            K[p][j] *= inv;
+            L1[p][j] *= inv;
+            Ki[p][j] *= inv;
+        }
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            if (r == p) continue;
+            const T fac = K[r][p];
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                K[r][j] -= fac * K[p][j];
+                L1[r][j] -= fac * L1[p][j];
+                Ki[r][j] -= fac * Ki[p][j];
+            }
+        }
+    }
+    T L2[S][S], rp[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
+        rp[i] = T(1);
+        if (relax == LBMS_RELAX_MAGIC) {
+            const T l = L1[i][i];
+            const T r8 = recip(l - T(8));
+            L2[i][i] = T(8) * (l - T(2)) * r8;  // Eq. 3-16
+            rp[i] = T(-48) * r8 * r8;           // its derivative
+        }
+    }
+    // (a) Lambda fixed: nu = Omega^T lambda, mu = lambda - nu + sum_k w_k nu_k
+    // (b) accumulators H = <lambda, odd(g)> + <lambda, even(g)> r
+    T Ga[S][S], Gs[S][S], wnu[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            Ga[i][j] = T(0);
+            Gs[i][j] = lam[i][0] * (f[j][0] - T(L::w(0)) * xi[j]);
+        }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        T nu0 = T(0);
+#pragma unroll
+        for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
+        mu[j][0] = lam[j][0] - nu0;
+        wnu[j] = T(L::w(0)) * nu0;
+    }
+#pragma unroll
+    for (int pr = 0; pr < L::NPAIR; ++pr) {
+        const int ka = 2 * pr + 1, kb = 2 * pr + 2;
+        const T wp = T(L::w(ka));
+        T ls[S], la[S], gs[S], ga[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            ls[i] = T(0.5) * (lam[i][ka] + lam[i][kb]);
+            la[i] = T(0.5) * (lam[i][ka] - lam[i][kb]);
+            gs[i] = T(0.5) * (f[i][ka] + f[i][kb]) - wp * xi[i];
+            ga[i] = T(0.5) * (f[i][ka] - f[i][kb]);
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            T ns = T(0), na = T(0);
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                ns += L2[i][j] * ls[i];
+                na += L1[i][j] * la[i];
+            }
+            mu[j][ka] = lam[j][ka] - (ns + na);
+            mu[j][kb] = lam[j][kb] - (ns - na);
+            wnu[j] += T(2) * wp * ns;
+        }
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                Ga[i][j] += T(2) * la[i] * ga[j];
+                Gs[i][j] += T(2) * ls[i] * gs[j];
+            }
+    }
+    // Z = K^{-T} H (I - Lambda_1/2)^T
+    T Y[S][S];
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            T acc = T(0);
+#pragma unroll
+            for (int d = 0; d < S; ++d) acc += Ki[d][a] * (Ga[d][c] + (d == c ? rp[d] : T(1)) * Gs[d][c]);
+            Y[a][c] = acc;
+        }
+    T Z[S][S];
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int b = 0; b < S; ++b) {
+            T acc = Y[a][b];
+#pragma unroll
+            for (int c = 0; c < S; ++c) acc -= T(0.5) * Y[a][c] * L1[b][c];
+            Z[a][b] = acc;
+        }
+    // (b) s_m with E_m = dB/dxi_m (closure included), added to every population of m
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (j != m) s += (invD[m][S] - invD[m][j]) * Z[m][j];
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+            if (i != m) s += (invD[i][m] - invD[i][S]) * Z[i][i];
+        const T add = wnu[m] - s;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) mu[m][k] += add;
+    }
+    // dL/dc_pq with F_pq = dB/dc_pq
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+        // pair {p, n-1}: row p of B, F[p][j] = xi_p (j != p), F[p][p] = xi_p + xi_n
+        T row = T(0);
+#pragma unroll
+        for (int j = 0; j < S; ++j) row += Z[p][j];
+        dc[pair_index(p, S, S)] += -(xi[p] * row + xi[S] * Z[p][p]);
+#pragma unroll
+        for (int q = p + 1; q < S; ++q) {
+            // pair {p, q}, both evolved: F[p][q] = -xi_p, F[q][p] = -xi_q,
+            // F[p][p] = xi_q, F[q][q] = xi_p
+            dc[pair_index(p, q, S)] +=
+                -(-xi[p] * Z[p][q] - xi[q] * Z[q][p] + xi[q] * Z[p][p] + xi[p] * Z[q][q]);
+        }
+    }
+}
+
+template <typename T>
+struct AdjParams {
+    const T* __restrict__ fprev;  // f+(t-1)
+    const T* __restrict__ lam_in;  // lambda(t)
+    T* __restrict__ lam_out;       // lambda(t-1)
+    double* gacc;                  // [blocks][npairs] accumulated dL/dc (FP64)
+    Geom g;
+    int relax;
+    Coeffs<T> co;
+};
+
+// One adjoint step.  Each thread: gather f(t) as the forward did, form mu at its
+// node, and write mu back to the slots the forward gather read (P^T).
+template <int LAT, int S, typename T>
+__global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
+{
+    using L = Lattice<LAT>;
+    constexpr int Q = L::Q;
+    constexpr int NP = NPairs<S>::value;
+    const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
+    const bool active = cell < p.g.cells;
+    T dc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) dc[q] = T(0);
+    if (active) {
+        const Neighbourhood h = neighbourhood(p.g, cell);
+        T f[S][Q], lam[S][Q], mu[S][Q];
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, f);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int k = 0; k < Q; ++k) lam[s][k] = p.lam_in[(size_t)(s * Q + k) * p.g.cells + cell];
+        adjoint_node<LAT, S, T>(f, lam, p.co.invD, T(1.0 / L::cs2()), p.relax, mu, dc);
+        // scatter through the gather's source slots
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
+            int32_t off = 0;
+            bool bounce = false;
+            if (cx != 0) { off += h.ox[cx > 0 ? 0 : 1]; bounce |= h.bx[cx > 0 ? 0 : 1]; }
+            if (cy != 0) { off += h.oy[cy > 0 ? 0 : 1]; bounce |= h.by[cy > 0 ? 0 : 1]; }
+            if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
+            const uint32_t dst = bounce ? cell : (uint32_t)((int32_t)cell + off);
+            const size_t plane = (size_t)(bounce ? opp(k) : k) * p.g.cells;
+#pragma unroll
+            for (int s = 0; s < S; ++s) p.lam_out[(size_t)s * Q * p.g.cells + plane + dst] = mu[s][k];
+        }
+    }
+    // per-block sums of dL/dc, accumulated over steps in FP64 by the block's slot
+    __shared__ float red[kBlock / 32];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        float v = (float)dc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) p.gacc[(size_t)blockIdx.x * NP + q] += (double)v;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+struct AdjFieldParams {
+    const T* grad_x;  // seed: dL/dxi(T) [n][cells]
+    T* lam;           // seed: lambda(T) [S][Q][cells]; initial: lambda(0)
+    T* grad_x0;       // initial: dL/dx0 [n][cells]
+    uint32_t cells;
+};
+
+// lambda(T)_k^i = dL/dxi_i - dL/dxi_n (xi_i = sum_k f+_k^i, xi_n = 1 - sum_i xi_i)
+template <int LAT, int S, typename T>
+__global__ void __launch_bounds__(kBlock) k_adjoint_seed(AdjFieldParams<T> p)
+{
+    constexpr int Q = Lattice<LAT>::Q;
+    const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.cells) return;
+    const T gn = p.grad_x[(size_t)S * p.cells + cell];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const T v = p.grad_x[(size_t)s * p.cells + cell] - gn;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) p.lam[(size_t)(s * Q + k) * p.cells + cell] = v;
+    }
+}
+
+// dL/dx0_i = sum_k w_k lambda(0)_k^i for the evolved species (f+(0) = w_k xi(0));
+// the closure species does not enter the model: its entry is zero.
+template <int LAT, int S, typename T>
+__global__ void __launch_bounds__(kBlock) k_adjoint_initial(AdjFieldParams<T> p)
+{
+    using L = Lattice<LAT>;
+    constexpr int Q = L::Q;
+    const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.cells) return;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc += T(L::w(k)) * p.lam[(size_t)(s * Q + k) * p.cells + cell];
+        p.grad_x0[(size_t)s * p.cells + cell] = acc;
+    }
+    p.grad_x0[(size_t)S * p.cells + cell] = T(0);
+}
+
+enum AdjOp : int { AOP_STEP = 0, AOP_SEED = 1, AOP_INITIAL = 2 };
+
+struct AArgs {
+    const void* fprev = nullptr;
+    const void* lam_in = nullptr;
+    void* lam_out = nullptr;
+    double* gacc = nullptr;
+    const void* grad_x = nullptr;
+    void* grad_x0 = nullptr;
+    void* lam = nullptr;
+    KArgs k;  // geometry, faces, relaxation, diffusivities, stream
+};
+
+template <int LAT, int S, typename T>
+cudaError_t adj_launch(AdjOp op, const AArgs& a)
+{
+    const uint32_t blocks = node_blocks(a.k.cells);
+    if (op == AOP_STEP) {
+        AdjParams<T> p;
+        p.fprev = static_cast<const T*>(a.fprev);
+        p.lam_in = static_cast<const T*>(a.lam_in);
+        p.lam_out = static_cast<T*>(a.lam_out);
+        p.gacc = a.gacc;
+        p.g = make_geom(a.k);
+        p.relax = a.k.relax;
+        p.co = make_coeffs<T>(a.k);
+        k_adjoint_step<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
+        return cudaGetLastError();
+    }
+    AdjFieldParams<T> p;
+    p.grad_x = static_cast<const T*>(a.grad_x);
+    p.lam = static_cast<T*>(a.lam);
+    p.grad_x0 = static_cast<T*>(a.grad_x0);
+    p.cells = a.k.cells;
+    if (op == AOP_SEED)
+        k_adjoint_seed<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
+    else
+        k_adjoint_initial<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <int LAT, typename T>
+cudaError_t adj_dispatch_S(AdjOp op, const AArgs& a)
+{
+    switch (a.k.n_species - 1) {
+        case 1: return adj_launch<LAT, 1, T>(op, a);
+        case 2: return adj_launch<LAT, 2, T>(op, a);
+        case 3: return adj_launch<LAT, 3, T>(op, a);
+        case 4: return adj_launch<LAT, 4, T>(op, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LAT>
+cudaError_t adj_dispatch_lattice(AdjOp op, int dtype, const AArgs& a)
+{
+    return dtype == LBMS_F64 ? adj_dispatch_S<LAT, double>(op, a) : adj_dispatch_S<LAT, float>(op, a);
+}
+
+cudaError_t adj_dispatch_d2q5(AdjOp op, int dtype, const AArgs& a);
+cudaError_t adj_dispatch_d2q9(AdjOp op, int dtype, const AArgs& a);
+cudaError_t adj_dispatch_d3q7(AdjOp op, int dtype, const AArgs& a);
+
+}  // namespace lbms

@@ -9,6 +9,7 @@
 
 #include <new>
 
+#include "adjoint.cuh"
 #include "lbms_internal.h"
 #include "node.cuh"
 
@@ -113,6 +114,25 @@ __global__ void k_mass_finalize_pairs(const double2* __restrict__ partials, uint
     }
 }
 
+__global__ void k_set_word(uint32_t* w, uint32_t v) { *w = v; }
+
+struct GradScale {
+    double v[16];  // 1 / D_pq^2 per pair
+};
+
+// dL/dD_pq = -(1/D_pq^2) sum over blocks of the accumulated dL/dc_pq (c = 1/D),
+// one block per pair, fixed order.
+__global__ void k_adjoint_reduce(const double* __restrict__ gacc, uint32_t blocks, int np, GradScale gs,
+                                 double* __restrict__ out)
+{
+    __shared__ double2 red[kBlock / 32];
+    const int q = blockIdx.x;
+    double sum = 0.0, comp = 0.0;
+    for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x) two_sum_add(sum, comp, gacc[(size_t)b * np + q]);
+    block_reduce_pair(sum, comp, red);
+    if (threadIdx.x == 0) out[q] = -(sum + comp) * gs.v[q];
+}
+
 // Fraction bits of the fixed-point mass partials: the sum of |xi| <= 4 over all
 // nodes must stay below 2^62.
 int fixed_shift_for(uint32_t cells)
@@ -175,6 +195,15 @@ cudaError_t dispatch(const lbms_t* h, Op op, const KArgs& a)
         case LBMS_D2Q5: return dispatch_d2q5(op, h->dtype, a);
         case LBMS_D2Q9: return dispatch_d2q9(op, h->dtype, a);
         default: return dispatch_d3q7(op, h->dtype, a);
+    }
+}
+
+cudaError_t adj_dispatch(const lbms_t* h, AdjOp op, const AArgs& a)
+{
+    switch (h->lattice) {
+        case LBMS_D2Q5: return adj_dispatch_d2q5(op, h->dtype, a);
+        case LBMS_D2Q9: return adj_dispatch_d2q9(op, h->dtype, a);
+        default: return adj_dispatch_d3q7(op, h->dtype, a);
     }
 }
 
@@ -535,6 +564,105 @@ int lbms_status(lbms_t* h, uint32_t* flags)
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (status)");
     e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaStreamSynchronize");
+}
+
+int lbms_get_state(lbms_t* h, void* f_out)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!f_out) return fail(h, LBMS_EINVAL, "f_out is NULL");
+    const size_t bytes = (size_t)h->S * h->Q * h->cells * h->es;
+    cudaError_t e = cudaMemcpyAsync(f_out, h->f[h->cur], bytes, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess && !is_device_ptr(f_out)) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaMemcpyAsync (state)");
+}
+
+int lbms_set_state_raw(lbms_t* h, const void* f_in, long step)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!f_in) return fail(h, LBMS_EINVAL, "f_in is NULL");
+    if (step < 0) return fail(h, LBMS_EINVAL, "step = %ld is negative", step);
+    const size_t bytes = (size_t)h->S * h->Q * h->cells * h->es;
+    cudaError_t e = cudaMemcpyAsync(h->f[0], f_in, bytes, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) {
+        k_set_word<<<1, 1, 0, h->stream>>>(h->clock, (uint32_t)step);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !is_device_ptr(f_in)) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "raw state upload");
+    h->cur = 0;
+    h->steps = step;
+    h->mass_valid = false;
+    return LBMS_OK;
+}
+
+size_t lbms_adjoint_scratch_size(const lbms_t* h)
+{
+    if (!h || h->S > 4) return 0;
+    return (size_t)h->blocks * (h->n * (h->n - 1) / 2) * sizeof(double);
+}
+
+int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
+{
+    if (!h) return LBMS_EINVAL;
+    if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (!grad_x || !lam) return fail(h, LBMS_EINVAL, "grad_x and lam must not be NULL");
+    AArgs a;
+    a.k = base_args(h, h->stream);
+    a.grad_x = grad_x;
+    a.lam = lam;
+    cudaError_t e = adj_dispatch(h, AOP_SEED, a);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "adjoint seed kernel");
+}
+
+int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* lam_out, void* gacc)
+{
+    if (!h) return LBMS_EINVAL;
+    if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (!f_prev || !lam_in || !lam_out || !gacc)
+        return fail(h, LBMS_EINVAL, "f_prev, lam_in, lam_out and gacc must not be NULL");
+    if (lam_in == lam_out) return fail(h, LBMS_EINVAL, "lam_in and lam_out must be different buffers");
+    AArgs a;
+    a.k = base_args(h, h->stream);
+    a.fprev = f_prev;
+    a.lam_in = lam_in;
+    a.lam_out = lam_out;
+    a.gacc = static_cast<double*>(gacc);
+    cudaError_t e = adj_dispatch(h, AOP_STEP, a);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "adjoint step kernel");
+}
+
+int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
+{
+    if (!h) return LBMS_EINVAL;
+    if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (!lam0 || !grad_x0) return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must not be NULL");
+    AArgs a;
+    a.k = base_args(h, h->stream);
+    a.lam = const_cast<void*>(lam0);
+    a.grad_x0 = grad_x0;
+    cudaError_t e = adj_dispatch(h, AOP_INITIAL, a);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "adjoint initial kernel");
+}
+
+int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
+{
+    if (!h) return LBMS_EINVAL;
+    if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (!gacc || !dL_dD) return fail(h, LBMS_EINVAL, "gacc and dL_dD must not be NULL");
+    const int np = h->n * (h->n - 1) / 2;
+    double* slot = reinterpret_cast<double*>(reinterpret_cast<char*>(h->status) + 128);
+    double invD2[16];
+    int k = 0;
+    for (int p = 0; p < h->n; ++p)
+        for (int q = p + 1; q < h->n; ++q, ++k) invD2[k] = h->invD[p][q] * h->invD[p][q];
+    GradScale gs;
+    for (int i = 0; i < np; ++i) gs.v[i] = invD2[i];
+    k_adjoint_reduce<<<np, kBlock, 0, h->stream>>>(static_cast<const double*>(gacc), h->blocks, np, gs, slot);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dL_dD, slot, sizeof(double) * np, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "adjoint reduction");
 }
 
 long lbms_steps_done(const lbms_t* h) { return h ? h->steps : -1; }

@@ -43,6 +43,8 @@ EXPORTED = (
     "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_schedule",
     "lbms_batch_get_schedule", "lbms_batch_tune", "lbms_batch_steps_done",
     "lbms_batch_last_error", "lbms_batch_destroy",
+    "lbms_get_state", "lbms_set_state_raw", "lbms_adjoint_scratch_size", "lbms_adjoint_seed",
+    "lbms_adjoint_step", "lbms_adjoint_initial", "lbms_adjoint_reduce",
 )
 BATCH_CANDIDATES = 7
 
@@ -96,6 +98,20 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_last_error.restype = ctypes.c_char_p
         L.lbms_destroy.argtypes = [P]
         L.lbms_destroy.restype = None
+        L.lbms_get_state.argtypes = [P, P]
+        L.lbms_get_state.restype = I
+        L.lbms_set_state_raw.argtypes = [P, P, ctypes.c_long]
+        L.lbms_set_state_raw.restype = I
+        L.lbms_adjoint_scratch_size.argtypes = [P]
+        L.lbms_adjoint_scratch_size.restype = SZ
+        L.lbms_adjoint_seed.argtypes = [P, P, P]
+        L.lbms_adjoint_seed.restype = I
+        L.lbms_adjoint_step.argtypes = [P, P, P, P, P]
+        L.lbms_adjoint_step.restype = I
+        L.lbms_adjoint_initial.argtypes = [P, P, P]
+        L.lbms_adjoint_initial.restype = I
+        L.lbms_adjoint_reduce.argtypes = [P, P, P]
+        L.lbms_adjoint_reduce.restype = I
         L.lbms_batch_workspace_size.argtypes = [I, I, I, P, I]
         L.lbms_batch_workspace_size.restype = SZ
         L.lbms_batch_create.argtypes = [P, I, I, I, P, P, I, P, I, P, SZ, P]
@@ -288,6 +304,55 @@ class Solver:
 
     def mass(self) -> np.ndarray:
         return lbms_mass(self._h, self.n)
+
+    @property
+    def state_shape(self):
+        nx, ny, nz = self.grid
+        return (self.n - 1, Q_OF[self.lattice], nx * ny * nz)
+
+    def get_state(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Copy of the post-collision populations [n - 1, Q, cells] (a checkpoint)."""
+        if out is None:
+            out = torch.empty(self.state_shape, dtype=self.dtype, device=self.device)
+        _check(self._h, load().lbms_get_state(self._h, ctypes.c_void_p(out.data_ptr())), "lbms_get_state")
+        return out
+
+    def set_state_raw(self, f: torch.Tensor, step: int) -> None:
+        """Load a checkpoint taken after ``step`` steps."""
+        f = self._field(f, self.state_shape)
+        _check(self._h, load().lbms_set_state_raw(self._h, ctypes.c_void_p(f.data_ptr()), int(step)),
+               "lbms_set_state_raw")
+        self._keep = f
+
+    def adjoint_scratch(self) -> torch.Tensor:
+        nbytes = int(load().lbms_adjoint_scratch_size(self._h))
+        if nbytes == 0:
+            raise LbmsError("the adjoint supports up to 5 species")
+        return torch.zeros(nbytes // 8, dtype=torch.float64, device=self.device)
+
+    def adjoint_seed(self, grad_x: torch.Tensor, lam: torch.Tensor) -> None:
+        grad_x = self._field(grad_x.contiguous(), self.field_shape)
+        _check(self._h, load().lbms_adjoint_seed(self._h, ctypes.c_void_p(grad_x.data_ptr()),
+                                                 ctypes.c_void_p(lam.data_ptr())), "lbms_adjoint_seed")
+
+    def adjoint_step(self, f_prev: torch.Tensor, lam_in: torch.Tensor, lam_out: torch.Tensor,
+                     gacc: torch.Tensor) -> None:
+        _check(self._h, load().lbms_adjoint_step(self._h, ctypes.c_void_p(f_prev.data_ptr()),
+                                                 ctypes.c_void_p(lam_in.data_ptr()),
+                                                 ctypes.c_void_p(lam_out.data_ptr()),
+                                                 ctypes.c_void_p(gacc.data_ptr())), "lbms_adjoint_step")
+
+    def adjoint_initial(self, lam0: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(self.field_shape, dtype=self.dtype, device=self.device)
+        _check(self._h, load().lbms_adjoint_initial(self._h, ctypes.c_void_p(lam0.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr())), "lbms_adjoint_initial")
+        return out
+
+    def adjoint_reduce(self, gacc: torch.Tensor) -> np.ndarray:
+        out = np.zeros(self.n * (self.n - 1) // 2, dtype=np.float64)
+        _check(self._h, load().lbms_adjoint_reduce(self._h, ctypes.c_void_p(gacc.data_ptr()),
+                                                   out.ctypes.data_as(ctypes.c_void_p)), "lbms_adjoint_reduce")
+        return out
 
     def populations(self) -> torch.Tensor:
         """View of the current population buffer, shape [n - 1, Q, cells]."""

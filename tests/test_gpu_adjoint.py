@@ -1,0 +1,159 @@
+"""Adjoint kernels and the differentiable solver (gradients with respect to
+the binary diffusivities and the initial field).
+
+1. One adjoint step is the transpose of the derivative of one forward step:
+   <J v, w> = <v, J^T w> with J v from central differences of the FP64
+   forward step, and the same for the derivative with respect to D_ij.
+2. Whole runs: the adjoint gradient of L = sum (x(T) - x*)^2 against central
+   finite differences of the FP64 CPU oracle on a 64 x 64 copy of the
+   512 x 512 workload (D pairs; the initial field along random directions),
+   and at full size against central differences of the GPU forward.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as sy
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
+
+torch = pytest.importorskip("torch")
+
+P, W = "periodic", "noflux"
+D_START = (0.10, 0.08, 0.02)
+D_TARGET = (0.09, 0.07, 0.02)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _one_step(s, f, step=0):
+    s.set_state_raw(f, step)
+    s.step(1)
+    return s.get_state()
+
+
+@pytest.mark.parametrize("lattice,n,dims,bc", [
+    ("D2Q5", 3, (21, 13, 1), (W, W, P, P, P, P)),
+    ("D2Q9", 4, (17, 11, 1), (P, P, W, W, P, P)),
+    ("D3Q7", 5, (9, 7, 6), (W, W, P, P, W, W)),
+    ("D2Q9", 2, (12, 9, 1), (P,) * 6),
+])
+def test_adjoint_step_is_transpose_of_step_derivative(lattice, n, dims, bc):
+    from paper_1808_06787_gb300 import Solver
+
+    D = sy.random_D(n, seed=31 + n)
+    s = Solver(lattice, D, dims, bc=bc, dtype=torch.float64)
+    x0 = sy.sin_modes(n, *dims, amp=0.1, seed=40 + n)
+    s.set_state(torch.from_numpy(x0).cuda())
+    s.step(3)  # a state off equilibrium
+    f = s.get_state()
+    g = torch.Generator(device="cpu").manual_seed(5)
+    v = torch.randn(f.shape, generator=g, dtype=torch.float64).cuda() * 1e-2
+    w = torch.randn(f.shape, generator=g, dtype=torch.float64).cuda()
+    eps = 1e-6
+    Jv = (_one_step(s, f + eps * v) - _one_step(s, f - eps * v)) / (2 * eps)
+    lam_out = torch.empty_like(w)
+    gacc = s.adjoint_scratch()
+    s.adjoint_step(f, w, lam_out, gacc)
+    lhs = float((Jv * w).sum())
+    rhs = float((v * lam_out).sum())
+    assert abs(lhs - rhs) <= 1e-7 * max(abs(lhs), 1e-12), (lhs, rhs)
+    # derivative with respect to each D pair of L = <w, step(f; D)>
+    gD = s.adjoint_reduce(gacc)
+    k = 0
+    for p_ in range(n):
+        for q in range(p_ + 1, n):
+            h = 1e-6
+            Dp, Dm = D.copy(), D.copy()
+            Dp[p_, q] = Dp[q, p_] = D[p_, q] + h
+            Dm[p_, q] = Dm[q, p_] = D[p_, q] - h
+            sp = Solver(lattice, Dp, dims, bc=bc, dtype=torch.float64)
+            sm = Solver(lattice, Dm, dims, bc=bc, dtype=torch.float64)
+            fd = float(((_one_step(sp, f) - _one_step(sm, f)) * w).sum()) / (2 * h)
+            assert abs(gD[k] - fd) <= 1e-6 * max(abs(fd), 1e-9) + 1e-9, (p_, q, gD[k], fd)
+            k += 1
+
+
+def _oracle_loss(D3, x0, target, steps):
+    import oracle
+
+    D = sy.D_from_pairs(3, {(1, 2): D3[0], (1, 3): D3[1], (2, 3): D3[2]})
+    x = oracle.run("D2Q5", D, x0, steps)
+    return float(((x - target) ** 2).sum())
+
+
+@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-6), (torch.float32, 2e-3)],
+                         ids=["f64", "f32"])
+def test_gradient_matches_oracle_finite_differences_64(dtype, rtol):
+    """64 x 64 copy of the 512 x 512 workload, 4000 steps, against the FP64 oracle."""
+    import oracle
+
+    from paper_1808_06787_gb300 import RunSpec, simulate
+
+    steps = 4000
+    x0 = sy.sin_modes(3, 64, 64, amp=0.05, seed=1005)
+    target = oracle.run("D2Q5", sy.D_from_pairs(3, {(1, 2): D_TARGET[0], (1, 3): D_TARGET[1],
+                                                    (2, 3): D_TARGET[2]}), x0, steps)
+    x0t = torch.from_numpy(x0).to(dtype).cuda().requires_grad_(True)
+    dp = torch.tensor(D_START, dtype=torch.float64, requires_grad=True)
+    spec = RunSpec("D2Q5", (64, 64, 1), steps, dtype=dtype)
+    xT = simulate(x0t, dp, spec)
+    loss = ((xT.double() - torch.from_numpy(target).cuda()) ** 2).sum()
+    loss.backward()
+    assert spec.stats["checkpoints"] == math.ceil(steps / math.ceil(math.sqrt(steps)))
+    gD = dp.grad.numpy()
+    h = 1e-4
+    for k in range(3):
+        up, dn = list(D_START), list(D_START)
+        up[k] += h
+        dn[k] -= h
+        fd = (_oracle_loss(up, x0, target, steps) - _oracle_loss(dn, x0, target, steps)) / (2 * h)
+        assert abs(gD[k] - fd) <= rtol * abs(fd) + 1e-12, (k, gD[k], fd)
+    # initial field along random directions that keep sum_sigma x0 = 1
+    gx = x0t.grad.double().cpu().numpy()
+    assert np.all(gx[2] == 0.0)
+    for seed in (1, 2):
+        r = sy.sin_modes(3, 64, 64, amp=1.0, seed=600 + seed)[0] - 1.0 / 3.0
+        v = np.stack([r, -r, np.zeros_like(r)])
+        eps = 1e-4
+        fd = (_oracle_loss(D_START, x0 + eps * v, target, steps)
+              - _oracle_loss(D_START, x0 - eps * v, target, steps)) / (2 * eps)
+        ad = float((gx * v).sum())
+        assert abs(ad - fd) <= rtol * abs(fd) + 1e-12, (seed, ad, fd)
+
+
+def test_config5_full_size_gradient_vs_finite_differences():
+    """512 x 512, 4000 steps, FP32: adjoint dL/dD against central differences
+    (h = 1e-4) of the GPU forward; target generated with D* = (0.09, 0.07, 0.02)."""
+    from paper_1808_06787_gb300 import RunSpec, Solver, simulate
+
+    steps = 4000
+    x0 = sy.sin_modes(3, 512, 512, amp=0.05, seed=1005)
+    x0t = torch.from_numpy(x0).float().cuda()
+
+    def forward(d3):
+        s = Solver("D2Q5", sy.D_from_pairs(3, {(1, 2): d3[0], (1, 3): d3[1], (2, 3): d3[2]}),
+                   (512, 512), dtype=torch.float32)
+        s.set_state(x0t)
+        s.step(steps)
+        return s.moments().double()
+
+    target = forward(D_TARGET)
+    dp = torch.tensor(D_START, dtype=torch.float64, requires_grad=True)
+    xT = simulate(x0t.clone().requires_grad_(True), dp, RunSpec("D2Q5", (512, 512, 1), steps))
+    loss = ((xT.double() - target) ** 2).sum()
+    loss.backward()
+    gD = dp.grad.numpy()
+    h = 1e-4
+    for k in range(3):
+        up, dn = list(D_START), list(D_START)
+        up[k] += h
+        dn[k] -= h
+        fd = (float(((forward(up) - target) ** 2).sum()) - float(((forward(dn) - target) ** 2).sum())) / (2 * h)
+        assert abs(gD[k] - fd) <= 1e-2 * abs(fd) + 1e-9, (k, gD[k], fd)
