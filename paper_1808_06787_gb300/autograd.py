@@ -84,7 +84,7 @@ class MaxwellStefanLB(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_xT: torch.Tensor):
         s = ctx.solver
-        lam = torch.empty(s.state_shape, dtype=s.dtype, device=s.device)
+        lam = torch.empty(s.state_shape, dtype=torch.float64, device=s.device)
         lam2 = torch.empty_like(lam)
         s.adjoint_seed(grad_xT.to(s.dtype), lam)
         gacc = s.adjoint_scratch()

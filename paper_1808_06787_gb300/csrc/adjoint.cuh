@@ -204,15 +204,20 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
     }
 }
 
+// The adjoint runs in FP64 for every solver precision: lambda is attenuated by
+// orders of magnitude over a long backward sweep while its updates are small
+// against it, so FP32 rounding of lambda accumulates coherently (as in the
+// forward, where it shifted species mass).  Forward states are read in the
+// solver's precision and promoted.
 template <typename T>
 struct AdjParams {
-    const T* __restrict__ fprev;  // f+(t-1)
-    const T* __restrict__ lam_in;  // lambda(t)
-    T* __restrict__ lam_out;       // lambda(t-1)
-    double* gacc;                  // [blocks][npairs] accumulated dL/dc (FP64)
+    const T* __restrict__ fprev;        // f+(t-1), solver precision
+    const double* __restrict__ lam_in;  // lambda(t)
+    double* __restrict__ lam_out;       // lambda(t-1)
+    double* gacc;                       // [blocks][npairs] accumulated dL/dc
     Geom g;
     int relax;
-    Coeffs<T> co;
+    Coeffs<double> co;
 };
 
 // One adjoint step.  Each thread: gather f(t) as the forward did, form mu at its
@@ -225,18 +230,22 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
     constexpr int NP = NPairs<S>::value;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
     const bool active = cell < p.g.cells;
-    T dc[NP];
+    double dc[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) dc[q] = T(0);
+    for (int q = 0; q < NP; ++q) dc[q] = 0.0;
     if (active) {
         const Neighbourhood h = neighbourhood(p.g, cell);
-        T f[S][Q], lam[S][Q], mu[S][Q];
-        pull<LAT, S, T>(p.fprev, p.g, cell, h, f);
+        T fs[S][Q];
+        double f[S][Q], lam[S][Q], mu[S][Q];
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, fs);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int k = 0; k < Q; ++k) lam[s][k] = p.lam_in[(size_t)(s * Q + k) * p.g.cells + cell];
-        adjoint_node<LAT, S, T>(f, lam, p.co.invD, T(1.0 / L::cs2()), p.relax, mu, dc);
+            for (int k = 0; k < Q; ++k) {
+                f[s][k] = (double)fs[s][k];
+                lam[s][k] = p.lam_in[(size_t)(s * Q + k) * p.g.cells + cell];
+            }
+        adjoint_node<LAT, S, double>(f, lam, p.co.invD, 1.0 / L::cs2(), p.relax, mu, dc);
         // scatter through the gather's source slots
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
@@ -252,21 +261,22 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
             for (int s = 0; s < S; ++s) p.lam_out[(size_t)s * Q * p.g.cells + plane + dst] = mu[s][k];
         }
     }
-    // per-block sums of dL/dc, accumulated over steps in FP64 by the block's slot
-    __shared__ float red[kBlock / 32];
+    // per-block sums of dL/dc in FP64 (the contributions of different nodes and
+    // steps cancel strongly), accumulated over steps in the block's own slot
+    __shared__ double red[kBlock / 32];
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        float v = (float)dc[q];
+        double v = (double)dc[q];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         if (lane == 0) red[warp] = v;
         __syncthreads();
         if (warp == 0) {
-            v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+            v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) p.gacc[(size_t)blockIdx.x * NP + q] += (double)v;
+            if (lane == 0) p.gacc[(size_t)blockIdx.x * NP + q] += v;
         }
         __syncthreads();
     }
@@ -274,9 +284,9 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
 
 template <typename T>
 struct AdjFieldParams {
-    const T* grad_x;  // seed: dL/dxi(T) [n][cells]
-    T* lam;           // seed: lambda(T) [S][Q][cells]; initial: lambda(0)
-    T* grad_x0;       // initial: dL/dx0 [n][cells]
+    const T* grad_x;  // seed: dL/dxi(T) [n][cells], solver precision
+    double* lam;      // seed: lambda(T) [S][Q][cells]; initial: lambda(0)
+    T* grad_x0;       // initial: dL/dx0 [n][cells], solver precision
     uint32_t cells;
 };
 
@@ -287,10 +297,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(AdjFieldParams<T> p)
     constexpr int Q = Lattice<LAT>::Q;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.cells) return;
-    const T gn = p.grad_x[(size_t)S * p.cells + cell];
+    const double gn = (double)p.grad_x[(size_t)S * p.cells + cell];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const T v = p.grad_x[(size_t)s * p.cells + cell] - gn;
+        const double v = (double)p.grad_x[(size_t)s * p.cells + cell] - gn;
 #pragma unroll
         for (int k = 0; k < Q; ++k) p.lam[(size_t)(s * Q + k) * p.cells + cell] = v;
     }
@@ -307,10 +317,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_initial(AdjFieldParams<T> p)
     if (cell >= p.cells) return;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        T acc = T(0);
+        double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) acc += T(L::w(k)) * p.lam[(size_t)(s * Q + k) * p.cells + cell];
-        p.grad_x0[(size_t)s * p.cells + cell] = acc;
+        for (int k = 0; k < Q; ++k) acc += L::w(k) * p.lam[(size_t)(s * Q + k) * p.cells + cell];
+        p.grad_x0[(size_t)s * p.cells + cell] = (T)acc;
     }
     p.grad_x0[(size_t)S * p.cells + cell] = T(0);
 }
@@ -335,18 +345,18 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
     if (op == AOP_STEP) {
         AdjParams<T> p;
         p.fprev = static_cast<const T*>(a.fprev);
-        p.lam_in = static_cast<const T*>(a.lam_in);
-        p.lam_out = static_cast<T*>(a.lam_out);
+        p.lam_in = static_cast<const double*>(a.lam_in);
+        p.lam_out = static_cast<double*>(a.lam_out);
         p.gacc = a.gacc;
         p.g = make_geom(a.k);
         p.relax = a.k.relax;
-        p.co = make_coeffs<T>(a.k);
+        p.co = make_coeffs<double>(a.k);
         k_adjoint_step<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
         return cudaGetLastError();
     }
     AdjFieldParams<T> p;
     p.grad_x = static_cast<const T*>(a.grad_x);
-    p.lam = static_cast<T*>(a.lam);
+    p.lam = static_cast<double*>(a.lam);
     p.grad_x0 = static_cast<T*>(a.grad_x0);
     p.cells = a.k.cells;
     if (op == AOP_SEED)
