@@ -467,6 +467,90 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Config 5: gradient of the L2 misfit of the final mole fractions (ternary
+    D2Q5, 512^2, FP32, 4000 steps, target from D* = (0.09, 0.07, 0.02)) with
+    respect to the three D_ij and the initial field, by the adjoint kernels
+    with sqrt(T) checkpointing; the cost is reported against the plain forward
+    run of the same steps."""
+    import numpy as np
+    import torch
+
+    import synthetic as sy
+    from paper_1808_06787_gb300 import RunSpec, Solver, simulate
+
+    steps = args.steps if args.steps != 20000 else 4000
+    n = 512 if args.grid == 256 else args.grid
+    x0 = torch.from_numpy(sy.sin_modes(3, n, n, amp=0.05, seed=1005)).float().cuda()
+    Dm = lambda d: sy.D_from_pairs(3, {(1, 2): d[0], (1, 3): d[1], (2, 3): d[2]})
+
+    def forward(d):
+        s = Solver("D2Q5", Dm(d), (n, n), dtype=torch.float32)
+        s.set_state(x0)
+        s.step(steps)
+        return s.moments()
+
+    target = forward((0.09, 0.07, 0.02)).double()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(max(1, args.warmup // 10)):
+        forward((0.10, 0.08, 0.02))
+    # one untimed gradient pass: loads torch's own kernels used by the loss
+    dpw = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
+    lw = ((simulate(x0.clone().requires_grad_(True), dpw, RunSpec("D2Q5", (n, n, 1), steps))
+           .double() - target) ** 2).sum()
+    lw.backward()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev[0].record()
+    forward((0.10, 0.08, 0.02))
+    ev[1].record()
+    dp = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
+    xg = x0.clone().requires_grad_(True)
+    spec = RunSpec("D2Q5", (n, n, 1), steps)
+    xT = simulate(xg, dp, spec)
+    loss = ((xT.double() - target) ** 2).sum()
+    ev[2].record()
+    loss.backward()
+    ev[3].record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_fwd = ev[0].elapsed_time(ev[1])
+    t_ckpt = ev[1].elapsed_time(ev[2])
+    t_bwd = ev[2].elapsed_time(ev[3])
+    out = {
+        "metric": "adjoint/fwd cost (gradient wrt D_ij and x0 over plain forward)",
+        "value": round((t_ckpt + t_bwd) / t_fwd, 3),
+        "unit": "x forward",
+        "n_gpus": 1,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": round((t_ckpt + t_bwd) / steps, 6),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 forward, f64 adjoint state",
+        "data": "synthetic (seeded sine modes; target from D* = (0.09, 0.07, 0.02))",
+        "config": {
+            "workload": "adjoint: ternary D2Q5 %d^2 FP32, %d steps, L2 misfit, gradients wrt 3 "
+                        "D_ij and the initial field, sqrt(T) checkpointing" % (n, steps),
+            "forward_ms": round(t_fwd, 3),
+            "checkpointed_forward_ms": round(t_ckpt, 3),
+            "backward_ms": round(t_bwd, 3),
+            "checkpoints": spec.stats.get("checkpoints"),
+            "segment_steps": spec.stats.get("segment"),
+            "dL_dD": [float(v) for v in dp.grad.numpy()],
+            "glups_forward": round(2.0 * n * n * steps / (t_fwd * 1e-3) / 1e9, 3),
+        },
+        "roofline": None,
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+
+
 def _oracle_sample_run(wl: Workload, cells_target: int, steps: int):
     """Time the oracle on a block of the workload with about cells_target nodes."""
     import oracle
@@ -552,7 +636,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tube", "blobs", "sine", "batch"], default="tube")
+    ap.add_argument("--workload", choices=["tube", "blobs", "sine", "batch", "adjoint"],
+                    default="tube")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -562,6 +647,13 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.workload == "adjoint":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no "
+                              "reference arm; use the single-solve workloads"}))
+        else:
+            run_adjoint(args)
+        return
     if args.workload == "batch":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no "

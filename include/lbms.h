@@ -213,10 +213,12 @@ int lbms_set_state_raw(lbms_t* h, const void* f_in, long step);
  * the initial field.  It differentiates the model's map f+(t-1) -> f+(t)
  * (propagation Eq. 3-13b, collision Eq. 3-13a with Lambda_1 from Eq. 3-26 and
  * Lambda_2 from Eq. 3-16, f_eq of Eq. 3-3) in exact arithmetic.  Up to 5
- * species.  All buffers are device memory.  The adjoint state lambda is FP64
- * for every solver dtype (FP32 rounding of lambda accumulates coherently over a
- * long backward sweep), with the population layout (S * Q * cells doubles);
- * f_prev, grad_x and grad_x0 have the handle's dtype.
+ * species.  All buffers are device memory.  The adjoint state lambda is stored
+ * in FP64 for every solver dtype (FP32 storage would lose its small per-step
+ * changes coherently over a long backward sweep), with the population layout
+ * (S * Q * cells doubles); f_prev, grad_x and grad_x0 have the handle's dtype.
+ * The per-node Jacobian runs in the handle's dtype on the deviation of lambda
+ * from its weighted mean over the directions, which the step maps to itself.
  *   lbms_adjoint_scratch_size  bytes of the gradient accumulator gacc
  *                              (FP64, per block and species pair); zero it
  *                              before the first step of a backward pass.

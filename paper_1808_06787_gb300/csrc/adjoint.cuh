@@ -204,11 +204,16 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
     }
 }
 
-// The adjoint runs in FP64 for every solver precision: lambda is attenuated by
-// orders of magnitude over a long backward sweep while its updates are small
-// against it, so FP32 rounding of lambda accumulates coherently (as in the
-// forward, where it shifted species mass).  Forward states are read in the
-// solver's precision and promoted.
+// Precision.  The adjoint state lambda is stored in FP64 for every solver
+// precision: over a long backward sweep lambda shrinks by orders of magnitude
+// while each step changes it little, so FP32 storage would lose the changes
+// coherently (as FP32 storage of f lost mass in the forward).  The per-node
+// map is linear in lambda and maps a lambda that is uniform over the
+// directions, lambda_k = lbar = sum_k w_k lambda_k, to itself exactly (its
+// odd and even parts of g have zero sums), so
+//     mu(lambda) = lbar + mu(d),   d = lambda - lbar,
+// and only d, which is small, goes through the Jacobian; that runs in the
+// solver's precision.  The FP64 work per node is forming lbar, d and lbar + mu(d).
 template <typename T>
 struct AdjParams {
     const T* __restrict__ fprev;        // f+(t-1), solver precision
@@ -217,7 +222,7 @@ struct AdjParams {
     double* gacc;                       // [blocks][npairs] accumulated dL/dc
     Geom g;
     int relax;
-    Coeffs<double> co;
+    Coeffs<T> co;
 };
 
 // One adjoint step.  Each thread: gather f(t) as the forward did, form mu at its
@@ -230,22 +235,32 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
     constexpr int NP = NPairs<S>::value;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
     const bool active = cell < p.g.cells;
-    double dc[NP];
+    T dc[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) dc[q] = 0.0;
+    for (int q = 0; q < NP; ++q) dc[q] = T(0);
     if (active) {
         const Neighbourhood h = neighbourhood(p.g, cell);
-        T fs[S][Q];
-        double f[S][Q], lam[S][Q], mu[S][Q];
-        pull<LAT, S, T>(p.fprev, p.g, cell, h, fs);
+        T f[S][Q], d[S][Q], mud[S][Q];
+        double lbar[S], mu[S][Q];
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, f);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            double lam[Q];
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                lam[k] = p.lam_in[(size_t)(s * Q + k) * p.g.cells + cell];
+                acc += L::w(k) * lam[k];
+            }
+            lbar[s] = acc;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) d[s][k] = (T)(lam[k] - acc);
+        }
+        adjoint_node<LAT, S, T>(f, d, p.co.invD, T(1.0 / L::cs2()), p.relax, mud, dc);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                f[s][k] = (double)fs[s][k];
-                lam[s][k] = p.lam_in[(size_t)(s * Q + k) * p.g.cells + cell];
-            }
-        adjoint_node<LAT, S, double>(f, lam, p.co.invD, 1.0 / L::cs2(), p.relax, mu, dc);
+            for (int k = 0; k < Q; ++k) mu[s][k] = lbar[s] + (double)mud[s][k];
         // scatter through the gather's source slots
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
@@ -350,7 +365,7 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
         p.gacc = a.gacc;
         p.g = make_geom(a.k);
         p.relax = a.k.relax;
-        p.co = make_coeffs<double>(a.k);
+        p.co = make_coeffs<T>(a.k);
         k_adjoint_step<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
         return cudaGetLastError();
     }
