@@ -202,21 +202,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def dist_context(backend: str = "nccl"):
+    """(world, rank, local_rank, dist-or-None) from the torchrun environment.
+
+    Every rank runs one independent replica of the workload (the solves share
+    no data), so the only collectives are the barriers around the timed region
+    and the maximum of the per-rank times."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def max_over_ranks(dist, values, device="cuda"):
+    """Element-wise maximum over ranks: the slowest replica sets the job time."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_rank: float, world: int, t_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job time."""
+    return units_per_rank * world / (t_ms * 1e-3)
+
+
 def run_ours(args, wl: Workload):
     import numpy as np
     import torch
 
     from paper_1808_06787_gb300 import Solver
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local, dist = dist_context()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
 
     def barrier():
         if dist is not None:
@@ -263,19 +290,15 @@ def run_ours(args, wl: Workload):
             barrier()
             e2e_s = time.perf_counter() - t0
 
-    t_ms = ms
     e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
-    if dist is not None:
-        tt = torch.tensor([ms, e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms, e2e_ms = tt.tolist()
+    t_ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms])
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     cells = wl.cells
     updates = float(wl.S) * cells * args.steps * world
-    glups = updates / (t_ms * 1e-3) / 1e9
+    glups = job_rate(float(wl.S) * cells * args.steps, world, t_ms) / 1e9
     bytes_per_launch = 2.0 * wl.S * wl.Q * wl.es * cells
     achieved = bytes_per_launch / (t_ms * 1e-3 / args.steps) / 1e9
     peak, peak_kind = hbm_peak()
@@ -348,15 +371,8 @@ def run_batch(args):
     import synthetic as sy
     from paper_1808_06787_gb300 import BatchSolver
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local, dist = dist_context()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
 
     def barrier():
         if dist is not None:
@@ -402,17 +418,13 @@ def run_batch(args):
             barrier()
             e2e_s = time.perf_counter() - t0
     e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
-    t_ms = ms
-    if dist is not None:
-        tt = torch.tensor([ms, e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms, e2e_ms = tt.tolist()
+    t_ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms])
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     nodes = float(sum(int(g[0]) * int(g[1]) for g in grids))
-    solves = count * world * args.steps / BATCH_SOLVE_STEPS / (t_ms * 1e-3)
+    solves = job_rate(count * args.steps / BATCH_SOLVE_STEPS, world, t_ms)
     glups = 2.0 * nodes * world * args.steps / (t_ms * 1e-3) / 1e9
     bytes_per_step = 2.0 * 2 * 5 * 4 * nodes
     achieved = bytes_per_step / (t_ms * 1e-3 / args.steps) / 1e9
