@@ -31,7 +31,7 @@ _lib = None
 
 LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2}
 RELAX = {"magic": 0, "srt": 1}
-BC = {"periodic": 0, "noflux": 1}
+BC = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 
 
 def build(force: bool = False) -> str:
@@ -66,8 +66,8 @@ def lib():
             L.orc_Dtilde.argtypes = [I, P, P, P]
             L.orc_lambdas.argtypes = [I, I, P, P, I, P, P]
             L.orc_collide_node.argtypes = [I, I, P, I, P, P]
-            L.orc_run.argtypes = [I, I, I, I, I, P, I, P, P, ctypes.c_long, P, P]
-            L.orc_run_snap.argtypes = [I, I, I, I, I, P, I, P, P, ctypes.c_long, P, P,
+            L.orc_run.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P]
+            L.orc_run_snap.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P,
                                        I, P, P]
             L.orc_set_threads.argtypes = [I]
             L.orc_get_threads.restype = I
@@ -159,10 +159,13 @@ def collide_node(lattice: str, D, fs, relax: str = "magic") -> np.ndarray:
 
 
 def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "magic",
-        flux: bool = False, snapshots=None):
+        flux: bool = False, snapshots=None, xb=None):
     """Run the scheme from f = f_eq(x0) for ``steps`` steps.
 
-    ``x0`` is [n, nz, ny, nx] (all n species).  Returns ``x`` of the same shape at
+    ``x0`` is [n, nz, ny, nx] (all n species).  ``bc`` names the six faces
+    (x-low, x-high, y-low, y-high, z-low, z-high) "periodic", "noflux" or
+    "dirichlet"; ``xb`` is [6, n], the composition held on each Dirichlet face
+    (rows of other faces are ignored).  Returns ``x`` of the same shape at
     t = steps; with ``flux=True`` also ``J`` of shape [n, dim, nz, ny, nx]; with
     ``snapshots`` (ascending step counts <= steps) also the mole-fraction fields
     at those steps, shape [len(snapshots), n, nz, ny, nx].
@@ -172,6 +175,8 @@ def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "
     n, nz, ny, nx = x0.shape
     q, dim = lattice_info(lattice)[:2]
     bcs = np.asarray([BC[b] if isinstance(b, str) else int(b) for b in bc], dtype=np.int32)
+    if xb is not None:
+        xb = _f64(np.nan_to_num(np.asarray(xb, dtype=np.float64)).reshape(6, n))
     xo = np.zeros_like(x0)
     Jo = np.zeros((n, dim, nz, ny, nx)) if flux else None
     if snapshots is not None:
@@ -180,12 +185,12 @@ def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "
             raise ValueError("snapshots must be ascending step counts within [0, steps]")
         so = np.zeros((snap.size,) + x0.shape)
         rc = lib().orc_run_snap(LATTICES[lattice], n, nx, ny, nz, _p(D), RELAX[relax], _p(bcs),
-                                _p(x0), int(steps), _p(xo), _p(Jo) if flux else None,
+                                None if xb is None else _p(xb), _p(x0), int(steps), _p(xo), _p(Jo) if flux else None,
                                 int(snap.size), _p(snap), _p(so))
     else:
         so = None
         rc = lib().orc_run(LATTICES[lattice], n, nx, ny, nz, _p(D), RELAX[relax], _p(bcs),
-                           _p(x0), int(steps), _p(xo), _p(Jo) if flux else None)
+                           None if xb is None else _p(xb), _p(x0), int(steps), _p(xo), _p(Jo) if flux else None)
     if rc != 0:
         raise RuntimeError("oracle run failed with code %d" % rc)
     out = [xo]

@@ -27,7 +27,12 @@
  *   7. Propagation, Eq. 3-13b, in the PUSH direction: f_k(x + c_k, t+1) = f+_k(x, t).
  *      Periodic faces wrap.  A no-flux face uses half-way bounce-back (Sec. 4):
  *      a population that would leave through it comes back to its own node in
- *      the opposite direction, f_kbar(x, t+1) = f+_k(x, t).
+ *      the opposite direction, f_kbar(x, t+1) = f+_k(x, t).  A Dirichlet face
+ *      of composition xi_b uses half-way anti-bounce-back (Sec. 4):
+ *      f_kbar(x, t+1) = -f+_k(x, t) + 2 w_k xi_{i,b} (w_k = w_kbar).  A link that
+ *      leaves through two or three faces at once (a D2Q9 diagonal at a corner)
+ *      takes the kind and composition of the first wall face in axis order x, y,
+ *      z; the paper does not treat corners.
  * Outputs (after the last step, at time t = steps): the mole fractions of all n
  * species and the diffusion fluxes.  The flux uses the local gradient of
  * Eq. xix, grad xi_i = -(1/c_s^2) sum_j lambda_1^{ij} sum_k c_k f_k^j (pre-
@@ -54,7 +59,7 @@
 
 enum { ORC_D2Q5 = 0, ORC_D2Q9 = 1, ORC_D3Q7 = 2 };
 enum { ORC_MAGIC = 0, ORC_SRT = 1 };
-enum { ORC_PERIODIC = 0, ORC_NOFLUX = 1 };
+enum { ORC_PERIODIC = 0, ORC_NOFLUX = 1, ORC_DIRICHLET = 2 };
 enum { GRP_CONSERVED = 0, GRP_ODD = 1, GRP_EVEN = 2 };
 
 typedef struct {
@@ -411,13 +416,17 @@ static void write_xi(const orc_lattice* L, int n, long cells, long per, const do
 /* As orc_run, and also records the mole fractions of all n species at the
  * ascending step counts snap_steps[0..n_snap) into snap_out[n_snap][n][cells]. */
 int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int relax,
-                 const int* bc, const double* x0, long steps, double* x_out, double* J_out,
-                 int n_snap, const long* snap_steps, double* snap_out)
+                 const int* bc, const double* xb, const double* x0, long steps, double* x_out,
+                 double* J_out, int n_snap, const long* snap_steps, double* snap_out)
 {
     orc_lattice L;
     if (n < 2 || n > ORC_MAXN || nx < 1 || ny < 1 || nz < 1 || steps < 0) return -1;
     if (lattice_init(lat, &L)) return -1;
     if (L.dim == 2 && nz != 1) return -1;
+    for (int a = 0; a < 6; ++a) {
+        if (bc[a] < ORC_PERIODIC || bc[a] > ORC_DIRICHLET) return -1;
+        if (bc[a] == ORC_DIRICHLET && !xb) return -1;
+    }
     for (int a = 0; a < 3; ++a)
         if ((bc[2 * a] == ORC_PERIODIC) != (bc[2 * a + 1] == ORC_PERIODIC)) return -1;
     const int S = n - 1, Q = L.Q;
@@ -451,20 +460,22 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
             if (node_collide(&L, n, D, relax, &f[c * per], fp)) { err |= 1; continue; }
             int pos[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
             for (int k = 0; k < Q; ++k) {
-                int dst[3], bounce = 0;
+                int dst[3], wall = -1;  /* first wall face the link leaves through */
                 for (int a = 0; a < 3; ++a) {
                     dst[a] = pos[a] + L.c[k][a];
-                    if (dst[a] < 0) {
-                        if (bc[2 * a] == ORC_NOFLUX) bounce = 1;
-                        else dst[a] += dims[a];
-                    } else if (dst[a] >= dims[a]) {
-                        if (bc[2 * a + 1] == ORC_NOFLUX) bounce = 1;
-                        else dst[a] -= dims[a];
-                    }
+                    int face = -1;
+                    if (dst[a] < 0) face = 2 * a;
+                    else if (dst[a] >= dims[a]) face = 2 * a + 1;
+                    if (face < 0) continue;
+                    if (bc[face] == ORC_PERIODIC) dst[a] += (face & 1) ? -dims[a] : dims[a];
+                    else if (wall < 0) wall = face;
                 }
                 for (int s = 0; s < S; ++s) {
-                    if (bounce)
+                    if (wall >= 0 && bc[wall] == ORC_NOFLUX)
                         g[c * per + s * Q + L.opp[k]] = fp[s * Q + k];
+                    else if (wall >= 0)
+                        g[c * per + s * Q + L.opp[k]] =
+                            -fp[s * Q + k] + 2.0 * L.w[k] * xb[wall * n + s];
                     else {
                         long d = ((long)dst[2] * ny + dst[1]) * nx + dst[0];
                         g[d * per + s * Q + k] = fp[s * Q + k];
@@ -517,12 +528,16 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
  * Run `steps` time steps from f = f_eq(x0) (Sec. 4, initialisation) and write the
  * mole fractions x_out[n][cells] and, if J_out is not NULL, the diffusion fluxes
  * J_out[n][dim][cells] at t = steps.  Fields are [z][y][x] with x fastest.
- * bc[6] = (x-low, x-high, y-low, y-high, z-low, z-high), each ORC_PERIODIC or
- * ORC_NOFLUX; a periodic axis must be periodic on both faces.  Returns 0, -1
- * for bad arguments, -2 for a singular Maxwell-Stefan matrix, -3 for no memory.
+ * bc[6] = (x-low, x-high, y-low, y-high, z-low, z-high), each ORC_PERIODIC,
+ * ORC_NOFLUX or ORC_DIRICHLET; a periodic axis must be periodic on both faces.
+ * xb[6][n] holds the boundary composition of each Dirichlet face (read only
+ * for those faces; may be NULL without one).  Returns 0, -1 for bad arguments,
+ * -2 for a singular Maxwell-Stefan matrix, -3 for no memory.
  */
 int orc_run(int lat, int n, int nx, int ny, int nz, const double* D, int relax,
-            const int* bc, const double* x0, long steps, double* x_out, double* J_out)
+            const int* bc, const double* xb, const double* x0, long steps, double* x_out,
+            double* J_out)
 {
-    return orc_run_snap(lat, n, nx, ny, nz, D, relax, bc, x0, steps, x_out, J_out, 0, NULL, NULL);
+    return orc_run_snap(lat, n, nx, ny, nz, D, relax, bc, xb, x0, steps, x_out, J_out, 0, NULL,
+                        NULL);
 }

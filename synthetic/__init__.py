@@ -40,6 +40,7 @@ __all__ = [
     "small_mode",
     "batch_instances",
     "batch_field",
+    "erf_step",
 ]
 
 
@@ -185,3 +186,16 @@ def batch_field(i: int, side: int, *, seed: int = 1004) -> np.ndarray:
     if i % 2 == 0:
         return sin_modes(3, side, side, amp=0.05, seed=seed * 7919 + i)
     return two_bulb(side, side, 1, width=4.0)
+
+
+def erf_step(nx: int, ny: int = 1, *, C0: float = 0.9, C1: float = 0.1,
+             half_width: float = 6.0) -> np.ndarray:
+    """Binary step of Sec. 4.1 on [-half_width, half_width] (cell centres):
+    xi_1 = C0 for x < 0 and C1 for x >= 0, xi_2 = 1 - xi_1."""
+    dx = 2.0 * half_width / nx
+    X = -half_width + (np.arange(nx) + 0.5) * dx
+    x1 = np.where(X < 0.0, C0, C1)
+    out = np.empty((2, 1, ny, nx))
+    out[0] = x1[None, None, :]
+    out[1] = 1.0 - out[0]
+    return out

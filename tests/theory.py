@@ -176,3 +176,49 @@ def theta_of(k, shape):
     nz, ny, nx = shape
     return np.array([2 * math.pi * k[0] / nx, 2 * math.pi * k[1] / ny,
                      2 * math.pi * k[2] / nz if nz > 1 else 0.0])
+
+
+def erf_solution(X, t, D, C0, C1):
+    """Two-component step on the infinite line (Sec. 4.1, Eq. 4-2): xi_1 and J_1."""
+    from scipy.special import erf
+
+    X = np.asarray(X, dtype=np.float64)
+    xi = 0.5 * (C0 + C1) + 0.5 * (C1 - C0) * erf(X / (2.0 * np.sqrt(D * t)))
+    J = -0.5 * (C1 - C0) * np.sqrt(D / (np.pi * t)) * np.exp(-X * X / (4.0 * D * t))
+    return xi, J
+
+
+def rel_l2(a, n):
+    """Relative L2 error E = ||a - n|| / ||a|| (Sec. 4)."""
+    a = np.asarray(a)
+    return float(np.sqrt(np.sum((a - n) ** 2) / np.sum(a ** 2)))
+
+
+def ternary_steady_profile(xL, xR, D12, D13, D23, X):
+    """Steady one-dimensional Maxwell-Stefan profile between two fixed compositions.
+
+    With no sources the flux J is uniform and d(xi)/dX = -D~(xi)^{-1} J
+    (Eq. 2-12 on [0, 1]); J is found by shooting from xL so that the profile ends
+    at xR.  Uses the closed form of D~ of Remark IV, not the solver's B.
+    """
+    from scipy.integrate import solve_ivp
+    from scipy.optimize import fsolve
+
+    xL = np.asarray(xL, dtype=np.float64)
+    xR = np.asarray(xR, dtype=np.float64)
+
+    def rhs(_, y):
+        xi = (y[0], y[1], 1.0 - y[0] - y[1])
+        return -np.linalg.solve(ternary_Dtilde_closed(xi, D12, D13, D23), rhs.J)
+
+    def shoot(J):
+        rhs.J = np.asarray(J)
+        sol = solve_ivp(rhs, (0.0, 1.0), xL[:2], rtol=1e-12, atol=1e-14)
+        return sol.y[:, -1] - xR[:2]
+
+    J0 = -ternary_Dtilde_closed(0.5 * (xL + xR), D12, D13, D23) @ (xR[:2] - xL[:2])
+    J = fsolve(shoot, J0, xtol=1e-13)
+    rhs.J = J
+    sol = solve_ivp(rhs, (0.0, 1.0), xL[:2], rtol=1e-12, atol=1e-14, dense_output=True)
+    y = sol.sol(np.asarray(X, dtype=np.float64))
+    return np.vstack([y, 1.0 - y.sum(axis=0)]), J
