@@ -53,8 +53,13 @@ enum { LBMS_D2Q5 = 0, LBMS_D2Q9 = 1, LBMS_D3Q7 = 2 };
 enum { LBMS_F32 = 0, LBMS_F64 = 1 };
 
 /* Face kinds.  PERIODIC wraps (used in all experiments of Sec. 4); NOFLUX is the
- * half-way bounce-back of Sec. 4, f_k(x_f, t+1) = f+_kbar(x_f, t). */
-enum { LBMS_PERIODIC = 0, LBMS_NOFLUX = 1 };
+ * half-way bounce-back of Sec. 4, f_k(x_f, t+1) = f+_kbar(x_f, t); DIRICHLET
+ * holds a fixed composition xi_b on the face by the half-way anti-bounce-back
+ * of Sec. 4, f_k(x_f, t+1) = -f+_kbar(x_f, t) + 2 w_kbar xi_{i,b} (set with
+ * lbms_set_boundary).  A D2Q9 diagonal link leaving through two wall faces at
+ * a corner takes the kind (and composition) of the first of them in axis
+ * order x, y, z. */
+enum { LBMS_PERIODIC = 0, LBMS_NOFLUX = 1, LBMS_DIRICHLET = 2 };
 
 /* Relaxation of the even moments.  MAGIC: Lambda_2 by Eq. 3-16 (off-diagonal
  * entries equal Lambda_1, diagonal 8 (l - 2) / (l - 8)).  SRT: Lambda_2 =
@@ -85,8 +90,9 @@ enum {
 /*
  * Bytes of device workspace that lbms_create needs for this problem: two
  * population buffers of S * Q * cells elements (ping-pong), per-block partial
- * sums for the mass diagnostic, a status word and a staging area (at most
- * 16 MiB) for host input/output.  Returns 0 for an invalid combination.
+ * sums for the mass diagnostic, a status word, the compositions of Dirichlet
+ * faces and a staging area (at most 16 MiB) for host input/output.  Returns 0
+ * for an invalid combination.
  */
 size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dtype);
 
@@ -102,8 +108,10 @@ size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dt
  *              finite, > 0 and symmetric (D_ij = D_ji); the diagonal is ignored.
  *   relax      LBMS_RELAX_MAGIC | LBMS_RELAX_SRT.
  *   bc         host array of 6 face kinds {x-low, x-high, y-low, y-high, z-low,
- *              z-high}; a periodic face must be paired with a periodic face on
- *              the same axis.  Unused z faces of a 2D lattice are ignored.
+ *              z-high}, each LBMS_PERIODIC, LBMS_NOFLUX or LBMS_DIRICHLET; a
+ *              periodic face must be paired with a periodic face on the same
+ *              axis.  Unused z faces of a 2D lattice are ignored.  Every
+ *              Dirichlet face needs lbms_set_boundary before the first step.
  *   dtype      LBMS_F32 | LBMS_F64.
  *   workspace  device memory of at least lbms_workspace_size() bytes, aligned
  *              to 256 bytes, owned by the caller and kept alive until
@@ -128,12 +136,27 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
 int lbms_set_state(lbms_t* h, const void* x0);
 
 /*
+ * Set the composition xi_b held on Dirichlet face `face` (0..5 in the order of
+ * bc; the face must have been created LBMS_DIRICHLET): xi_b is a host array of
+ * all n mole fractions, each in [0, 1] and summing to 1 within 1e-6 (the
+ * evolved species' values enter the anti-bounce-back rule of Sec. 4).  The
+ * values are copied to the workspace in stream order, so steps already queued
+ * keep the old composition and later steps see the new one (time-dependent
+ * boundaries).  Synchronises the stream; not callable during stream capture.
+ * Returns LBMS_EINVAL for a bad face or composition, LBMS_ECUDA if the copy
+ * fails.
+ */
+int lbms_set_boundary(lbms_t* h, int face, const double* xi_b);
+
+/*
  * Advance n_steps >= 0 time steps of Eqs. 3-13a/3-13b (pull form: each node
  * gathers f+_k(x - c_k), collides, and stores its post-collision populations).
  * The last step of each call also writes per-block partial sums of every
  * species' mole fraction and reduces them (see lbms_mass), so lbms_mass after
  * lbms_step reads no populations.  Asynchronous: launch errors are returned at once, numerical
- * trouble is raised in the status flags.
+ * trouble is raised in the status flags.  Returns LBMS_EINVAL if a Dirichlet
+ * face has no composition yet.  With Dirichlet faces the species' masses are
+ * not conserved (the faces exchange mass with the outside).
  */
 int lbms_step(lbms_t* h, long n_steps);
 

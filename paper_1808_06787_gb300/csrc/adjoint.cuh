@@ -222,6 +222,7 @@ struct AdjParams {
     double* gacc;                       // [blocks][npairs] accumulated dL/dc
     Geom g;
     int relax;
+    const T* __restrict__ xb;           // Dirichlet face compositions [6][S]
     Coeffs<T> co;
 };
 
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
         const Neighbourhood h = neighbourhood(p.g, cell);
         T f[S][Q], d[S][Q], mud[S][Q];
         double lbar[S], mu[S][Q];
-        pull<LAT, S, T>(p.fprev, p.g, cell, h, f);
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             double lam[Q];
@@ -261,7 +262,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int k = 0; k < Q; ++k) mu[s][k] = lbar[s] + (double)mud[s][k];
-        // scatter through the gather's source slots
+        // scatter through the gather's source slots; an anti-bounce-back link
+        // (Dirichlet face) entered the forward map with a factor -1
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
@@ -272,8 +274,14 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
             if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
             const uint32_t dst = bounce ? cell : (uint32_t)((int32_t)cell + off);
             const size_t plane = (size_t)(bounce ? opp(k) : k) * p.g.cells;
+            double sign = 1.0;
+            if (k != 0 && h.dir) {
+                const int wf = link_wall<LAT>(k, h);
+                if (wf >= 0 && ((h.dir >> wf) & 1u)) sign = -1.0;
+            }
 #pragma unroll
-            for (int s = 0; s < S; ++s) p.lam_out[(size_t)s * Q * p.g.cells + plane + dst] = mu[s][k];
+            for (int s = 0; s < S; ++s)
+                p.lam_out[(size_t)s * Q * p.g.cells + plane + dst] = sign * mu[s][k];
         }
     }
     // per-block sums of dL/dc in FP64 (the contributions of different nodes and
@@ -365,6 +373,7 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
         p.gacc = a.gacc;
         p.g = make_geom(a.k);
         p.relax = a.k.relax;
+        p.xb = static_cast<const T*>(a.k.xb);
         p.co = make_coeffs<T>(a.k);
         k_adjoint_step<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
         return cudaGetLastError();

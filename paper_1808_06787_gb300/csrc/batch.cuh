@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
         plane.cells = p.total_nodes;  // the gather's plane stride
         const uint32_t cell = d.base + local;
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, plane, cell, h, f);
+        pull<LAT, S, T>(p.fin, plane, cell, h, f, static_cast<const T*>(nullptr));
         mole_fractions<LAT, S, T>(f, xi);
         check_range<S, T>(xi, p.status);
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
         Geom plane = d.g;
         plane.cells = p.total_nodes;
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, plane, cell, h, f);
+        pull<LAT, S, T>(p.fin, plane, cell, h, f, static_cast<const T*>(nullptr));
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};

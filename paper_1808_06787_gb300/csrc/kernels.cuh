@@ -36,6 +36,7 @@ struct StepParams {
     // graph see the true step count
     const uint32_t* clock_in;
     uint32_t* clock_out;
+    const T* __restrict__ xb;  // Dirichlet face compositions [6][S]
     Coeffs<T> co;
 };
 
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<S, T>::value) k_step(Ste
     if (active) {
         const Neighbourhood h = neighbourhood(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, p.g, cell, h, f);
+        pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb);
         mole_fractions<LAT, S, T>(f, xi);
         check_range<S, T>(xi, p.status);
         T L1[S][S], L2[S][S];
@@ -197,6 +198,7 @@ struct FieldParams {
     uint32_t c0, c1, stride;
     int relax;
     uint32_t* status;
+    const T* xb;      // Dirichlet face compositions [6][S]
     Coeffs<T> co;
 };
 
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
     if (p.fprev) {
         const Neighbourhood h = neighbourhood(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fprev, p.g, cell, h, f);
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         T L1[S][S], L2[S][S];
@@ -328,7 +330,8 @@ inline Geom make_geom(const KArgs& a)
     g.nx = a.nx; g.ny = a.ny; g.nz = a.nz;
     g.nxy = (uint32_t)a.nx * (uint32_t)a.ny;
     g.cells = a.cells;
-    g.noflux = a.noflux;
+    g.noflux = a.noflux | a.dirichlet;
+    g.dirichlet = a.dirichlet;
     g.dnx = make_fastdiv((uint32_t)a.nx);
     g.dny = make_fastdiv((uint32_t)a.ny);
     return g;
@@ -348,6 +351,7 @@ cudaError_t launch(Op op, const KArgs& a)
         p.status = a.status;
         p.clock_in = a.clock_in;
         p.clock_out = a.clock_out;
+        p.xb = static_cast<const T*>(a.xb);
         p.co = make_coeffs<T>(a);
         const uint32_t blocks = node_blocks(a.cells);
         if (op == OP_STEP)
@@ -368,6 +372,7 @@ cudaError_t launch(Op op, const KArgs& a)
     p.c0 = a.c0; p.c1 = a.c1; p.stride = a.stride;
     p.relax = a.relax;
     p.status = a.status;
+    p.xb = static_cast<const T*>(a.xb);
     p.co = make_coeffs<T>(a);
     const uint32_t blocks = node_blocks(a.c1 - a.c0);
     if (blocks == 0) return cudaSuccess;

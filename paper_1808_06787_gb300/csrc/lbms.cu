@@ -27,8 +27,8 @@ int lattice_q(int lat) { return lat == LBMS_D2Q5 ? 5 : lat == LBMS_D2Q9 ? 9 : la
 int lattice_dim(int lat) { return lat == LBMS_D3Q7 ? 3 : 2; }
 
 struct Layout {
-    size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_staging, staging_bytes,
-        total;
+    size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_bound, off_staging,
+        staging_bytes, total;
 };
 
 bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
@@ -50,7 +50,8 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
     const size_t blocks = node_blocks((uint32_t)cells);
     L->off_mass = L->off_partials + align_up(blocks * n * sizeof(double2));
     L->off_status = L->off_mass + align_up(LBMS_MAX_SPECIES * sizeof(double));
-    L->off_staging = L->off_status + kAlign;
+    L->off_bound = L->off_status + kAlign;
+    L->off_staging = L->off_bound + align_up(6 * LBMS_MAX_SPECIES * sizeof(double));
     size_t want = (size_t)n * (1 + dim) * cells * es;
     L->staging_bytes = align_up(want < kStagingMax ? want : kStagingMax);
     L->total = L->off_staging + L->staging_bytes;
@@ -150,6 +151,9 @@ struct lbms_s {
     int nx = 1, ny = 1, nz = 1;
     uint32_t cells = 0, blocks = 0;
     uint32_t noflux = 0;
+    uint32_t dirichlet = 0;  // Dirichlet faces
+    uint32_t xb_set = 0;     // Dirichlet faces whose composition has been set
+    void* xb = nullptr;      // device [6][S] compositions of the Dirichlet faces, solver dtype
     size_t es = 4;
     double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};
     char* ws = nullptr;
@@ -213,6 +217,8 @@ KArgs base_args(const lbms_t* h, cudaStream_t st)
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
     a.cells = h->cells;
     a.noflux = h->noflux;
+    a.dirichlet = h->dirichlet;
+    a.xb = h->xb;
     a.relax = h->relax;
     a.n_species = h->n;
     memcpy(a.invD, h->invD, sizeof(a.invD));
@@ -345,15 +351,17 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
                 return fail(nullptr, LBMS_EINVAL, "D is not symmetric at (%d, %d)", i, j);
         }
     const int dim = lattice_dim(lattice);
-    uint32_t noflux = 0;
+    uint32_t noflux = 0, dirichlet = 0;
     for (int a = 0; a < dim; ++a) {
         const int lo = bc[2 * a], hi = bc[2 * a + 1];
-        if ((lo != LBMS_PERIODIC && lo != LBMS_NOFLUX) || (hi != LBMS_PERIODIC && hi != LBMS_NOFLUX))
+        if (lo < LBMS_PERIODIC || lo > LBMS_DIRICHLET || hi < LBMS_PERIODIC || hi > LBMS_DIRICHLET)
             return fail(nullptr, LBMS_EINVAL, "invalid face kind on axis %d", a);
         if ((lo == LBMS_PERIODIC) != (hi == LBMS_PERIODIC))
             return fail(nullptr, LBMS_EINVAL, "a periodic face must be paired on axis %d", a);
         if (lo == LBMS_NOFLUX) noflux |= 1u << (2 * a);
         if (hi == LBMS_NOFLUX) noflux |= 1u << (2 * a + 1);
+        if (lo == LBMS_DIRICHLET) dirichlet |= 1u << (2 * a);
+        if (hi == LBMS_DIRICHLET) dirichlet |= 1u << (2 * a + 1);
     }
     lbms_t* h = new (std::nothrow) lbms_t;
     if (!h) return fail(nullptr, LBMS_ENOMEM, "host allocation failed");
@@ -368,6 +376,7 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->cells = (uint32_t)((size_t)grid[0] * grid[1] * grid[2]);
     h->blocks = node_blocks(h->cells);
     h->noflux = noflux;
+    h->dirichlet = dirichlet;
     h->es = dtype == LBMS_F64 ? 8 : 4;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) h->invD[i][j] = i == j ? 0.0 : 1.0 / D[i * n + j];
@@ -381,6 +390,7 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->status = reinterpret_cast<uint32_t*>(h->ws + L.off_status);
     h->clock = h->status + 16;
     h->staging = h->ws + L.off_staging;
+    h->xb = h->ws + L.off_bound;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -434,10 +444,46 @@ int lbms_set_state(lbms_t* h, const void* x0)
     return LBMS_OK;
 }
 
+int lbms_set_boundary(lbms_t* h, int face, const double* xi_b)
+{
+    if (!h) return LBMS_EINVAL;
+    if (face < 0 || face > 5 || !((h->dirichlet >> face) & 1u))
+        return fail(h, LBMS_EINVAL, "face %d is not a Dirichlet face", face);
+    if (!xi_b) return fail(h, LBMS_EINVAL, "xi_b is NULL");
+    double sum = 0.0;
+    for (int s = 0; s < h->n; ++s) {
+        if (!isfinite(xi_b[s]) || xi_b[s] < -1e-6 || xi_b[s] > 1.0 + 1e-6)
+            return fail(h, LBMS_EINVAL, "xi_b[%d] = %g is not a mole fraction", s, xi_b[s]);
+        sum += xi_b[s];
+    }
+    if (fabs(sum - 1.0) > 1e-6)
+        return fail(h, LBMS_EINVAL, "the composition sums to %.9g, not 1", sum);
+    h->err[0] = '\0';
+    // stream-ordered: steps launched before this call see the old composition
+    double v64[LBMS_MAX_SPECIES];
+    float v32[LBMS_MAX_SPECIES];
+    for (int s = 0; s < h->S; ++s) {
+        v64[s] = xi_b[s];
+        v32[s] = (float)xi_b[s];
+    }
+    const void* src = h->dtype == LBMS_F64 ? static_cast<const void*>(v64) : static_cast<const void*>(v32);
+    cudaError_t e = cudaMemcpyAsync(static_cast<char*>(h->xb) + (size_t)face * h->S * h->es, src,
+                                    (size_t)h->S * h->es, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (boundary composition)");
+    // the copy reads pageable memory: wait for it before the locals go away
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    h->xb_set |= 1u << face;
+    return LBMS_OK;
+}
+
 int lbms_step(lbms_t* h, long n_steps)
 {
     if (!h) return LBMS_EINVAL;
     if (n_steps < 0) return fail(h, LBMS_EINVAL, "n_steps = %ld is negative", n_steps);
+    if (h->dirichlet & ~h->xb_set)
+        return fail(h, LBMS_EINVAL, "Dirichlet face mask 0x%x has no composition set",
+                    h->dirichlet & ~h->xb_set);
     h->err[0] = '\0';
     if (n_steps == 0) return LBMS_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -32,6 +32,8 @@ struct KArgs {
     uint32_t cells = 0;
     uint32_t c0 = 0, c1 = 0, stride = 0;  // cell range [c0, c1) and field stride (init, moments)
     uint32_t noflux = 0;                  // bit f set: face f is no-flux (x-, x+, y-, y+, z-, z+)
+    uint32_t dirichlet = 0;               // bit f set: face f is Dirichlet (fixed composition)
+    const void* xb = nullptr;             // Dirichlet compositions [6][S] in the solver's dtype
     int relax = LBMS_RELAX_MAGIC;
     int n_species = 2;
     double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};  // 1 / D_ij

@@ -220,15 +220,17 @@ struct FastDiv {
 struct Geom {
     int nx, ny, nz;
     uint32_t nxy, cells;
-    uint32_t noflux;  // bit f set: face f is no-flux (x-, x+, y-, y+, z-, z+)
+    uint32_t noflux;     // bit f set: face f is a wall, no-flux or Dirichlet (x-, x+, y-, y+, z-, z+)
+    uint32_t dirichlet;  // bit f set: wall face f holds a fixed composition
     FastDiv dnx, dny;
 };
 
 // Source offsets (in nodes) of the gather along each axis for c = +1 and c = -1,
-// with periodic wrap, and whether that source lies across a no-flux face.
+// with periodic wrap, and whether that source lies across a wall face.
 struct Neighbourhood {
     int32_t ox[2], oy[2], oz[2];  // [0]: c = +1 (source at -1), [1]: c = -1 (source at +1)
     bool bx[2], by[2], bz[2];
+    uint32_t dir;  // the Dirichlet faces this node lies on (bits as Geom::noflux)
 };
 
 __device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t cell)
@@ -254,16 +256,39 @@ __device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t c
     h.by[1] = yhi && (g.noflux & 8u);
     h.bz[0] = zlo && (g.noflux & 16u);
     h.bz[1] = zhi && (g.noflux & 32u);
+    h.dir = 0u;
+    if (g.dirichlet)  // uniform over the grid
+        h.dir = g.dirichlet & ((xlo ? 1u : 0u) | (xhi ? 2u : 0u) | (ylo ? 4u : 0u) |
+                               (yhi ? 8u : 0u) | (zlo ? 16u : 0u) | (zhi ? 32u : 0u));
     return h;
+}
+
+// The wall face the pull source of direction k lies across, or -1.  A D2Q9
+// diagonal at a corner can cross two walls: the first in axis order x, y, z
+// decides (the paper does not treat corners).
+template <int LAT>
+__device__ __forceinline__ int link_wall(int k, const Neighbourhood& h)
+{
+    using L = Lattice<LAT>;
+    const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
+    if (cx != 0 && h.bx[cx > 0 ? 0 : 1]) return cx > 0 ? 0 : 1;
+    if (cy != 0 && h.by[cy > 0 ? 0 : 1]) return cy > 0 ? 2 : 3;
+    if (cz != 0 && h.bz[cz > 0 ? 0 : 1]) return cz > 0 ? 4 : 5;
+    return -1;
 }
 
 // Gather f_k(x, t) = f+_k(x - c_k, t-1) for every species and direction: the
 // propagation of Eq. 3-13b read in the pull direction.  A source across a
 // periodic face wraps; a source across a no-flux face is replaced by the node's
-// own opposite population, f_k(x) = f+_kbar(x) (half-way bounce-back, Sec. 4).
+// own opposite population, f_k(x) = f+_kbar(x) (half-way bounce-back, Sec. 4);
+// across a Dirichlet face of composition xi_b by f_k(x) = -f+_kbar(x) +
+// 2 w_k xi_{s,b} (half-way anti-bounce-back, Sec. 4).  xb holds the evolved
+// species' compositions of the six faces, [6][S]; it is read only on nodes
+// next to a Dirichlet face.
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, uint32_t cell,
-                                     const Neighbourhood& h, T (&f)[S][Lattice<LAT>::Q])
+                                     const Neighbourhood& h, T (&f)[S][Lattice<LAT>::Q],
+                                     const T* __restrict__ xb)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
@@ -279,6 +304,16 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
         const size_t plane = (size_t)(bounce ? opp(k) : k) * g.cells;
 #pragma unroll
         for (int s = 0; s < S; ++s) f[s][k] = fin[(size_t)s * Q * g.cells + plane + src];
+    }
+    if (h.dir) {
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            const int wf = link_wall<LAT>(k, h);
+            if (wf >= 0 && ((h.dir >> wf) & 1u)) {
+#pragma unroll
+                for (int s = 0; s < S; ++s) f[s][k] = T(2.0 * L::w(k)) * xb[wf * S + s] - f[s][k];
+            }
+        }
     }
 }
 

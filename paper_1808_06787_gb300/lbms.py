@@ -26,7 +26,7 @@ LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2}
 DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3}
 Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7}
 RELAX = {"magic": 0, "srt": 1}
-FACE = {"periodic": 0, "noflux": 1}
+FACE = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 DTYPES = {torch.float32: 0, torch.float64: 1}
 
 LBMS_OK = 0
@@ -36,7 +36,8 @@ FLAG_INIT = 0x4
 ERRORS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ERANGE", 6: "ETIMEOUT"}
 
 EXPORTED = (
-    "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_step", "lbms_moments",
+    "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_set_boundary", "lbms_step",
+    "lbms_moments",
     "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_last_error",
     "lbms_destroy",
     "lbms_batch_workspace_size", "lbms_batch_create", "lbms_batch_set_state", "lbms_batch_step",
@@ -82,6 +83,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_create.restype = I
         L.lbms_set_state.argtypes = [P, P]
         L.lbms_set_state.restype = I
+        L.lbms_set_boundary.argtypes = [P, I, P]
+        L.lbms_set_boundary.restype = I
         L.lbms_step.argtypes = [P, ctypes.c_long]
         L.lbms_step.restype = I
         L.lbms_moments.argtypes = [P, P, P]
@@ -184,6 +187,12 @@ def lbms_set_state(h, x0_ptr: int) -> None:
     _check(h, load().lbms_set_state(h, ctypes.c_void_p(x0_ptr)), "lbms_set_state")
 
 
+def lbms_set_boundary(h, face: int, xi_b) -> None:
+    v = np.ascontiguousarray(np.asarray(xi_b, dtype=np.float64).reshape(-1))
+    _check(h, load().lbms_set_boundary(h, int(face), v.ctypes.data_as(ctypes.c_void_p)),
+           "lbms_set_boundary")
+
+
 def lbms_step(h, n_steps: int) -> None:
     _check(h, load().lbms_step(h, int(n_steps)), "lbms_step")
 
@@ -235,14 +244,16 @@ class Solver:
 
     ``lattice``: "D2Q5" | "D2Q9" | "D3Q7"; ``D``: n x n binary diffusivities in
     lattice units; ``grid``: (nx, ny[, nz]); ``bc``: one kind for all faces or six
-    kinds (x-, x+, y-, y+, z-, z+); ``relax``: "magic" (Eq. 3-16) or "srt";
+    kinds (x-, x+, y-, y+, z-, z+), each "periodic", "noflux" or "dirichlet";
+    ``boundary``: {face index: composition of all n species} for the Dirichlet
+    faces (see ``set_boundary``); ``relax``: "magic" (Eq. 3-16) or "srt";
     ``dtype``: torch.float32 or torch.float64.  Work is ordered on ``stream``
     (default: the current torch stream of ``device``).
     """
 
     def __init__(self, lattice: str, D, grid: Sequence[int], *, bc="periodic",
                  relax: str = "magic", dtype=torch.float32, device="cuda",
-                 stream: Optional[torch.cuda.Stream] = None):
+                 stream: Optional[torch.cuda.Stream] = None, boundary=None):
         if not torch.cuda.is_available():
             raise LbmsError("the lbms solver needs a CUDA device")
         self.lattice = lattice
@@ -262,6 +273,13 @@ class Solver:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self._h = lbms_create(lat, self.n, self.grid, self.D, RELAX[relax], bc, dt,
                               self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        for face, xi_b in (boundary or {}).items():
+            self.set_boundary(face, xi_b)
+
+    def set_boundary(self, face: int, xi_b) -> None:
+        """Composition (all n species) held on Dirichlet face ``face`` (0..5 as in
+        ``bc``); applies to the steps issued after this call."""
+        lbms_set_boundary(self._h, face, xi_b)
 
     @property
     def field_shape(self):

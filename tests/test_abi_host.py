@@ -95,8 +95,10 @@ def test_create_validates_before_device_work(lib):
     assert rc == 1
     rc, _, msg = _create(lib, bc=(0, 1, 0, 0, 0, 0))
     assert rc == 1 and "paired" in msg
-    rc, _, msg = _create(lib, bc=(2, 2, 0, 0, 0, 0))
-    assert rc == 1
+    rc, _, msg = _create(lib, bc=(3, 3, 0, 0, 0, 0))  # unknown face kind
+    assert rc == 1 and "face kind" in msg
+    rc, _, msg = _create(lib, bc=(2, 0, 0, 0, 0, 0))  # Dirichlet against a periodic face
+    assert rc == 1 and "paired" in msg
     rc, _, msg = _create(lib, relax=5)
     assert rc == 1 and "relaxation" in msg
     rc, _, msg = _create(lib, ws=0)
@@ -114,6 +116,7 @@ def test_create_validates_before_device_work(lib):
 def test_null_handle_calls(lib):
     assert lib.lbms_step(None, 1) == 1
     assert lib.lbms_set_state(None, None) == 1
+    assert lib.lbms_set_boundary(None, 0, None) == 1
     assert lib.lbms_moments(None, None, None) == 1
     assert lib.lbms_mass(None, None) == 1
     assert lib.lbms_status(None, None) == 1
