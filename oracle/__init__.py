@@ -66,8 +66,8 @@ def lib():
             L.orc_Dtilde.argtypes = [I, P, P, P]
             L.orc_lambdas.argtypes = [I, I, P, P, I, P, P]
             L.orc_collide_node.argtypes = [I, I, P, I, P, P]
-            L.orc_run.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P]
-            L.orc_run_snap.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P,
+            L.orc_run.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P, P]
+            L.orc_run_snap.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P, P,
                                        I, P, P]
             L.orc_set_threads.argtypes = [I]
             L.orc_get_threads.restype = I
@@ -159,7 +159,7 @@ def collide_node(lattice: str, D, fs, relax: str = "magic") -> np.ndarray:
 
 
 def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "magic",
-        flux: bool = False, snapshots=None, xb=None):
+        flux: bool = False, snapshots=None, xb=None, grad: bool = False):
     """Run the scheme from f = f_eq(x0) for ``steps`` steps.
 
     ``x0`` is [n, nz, ny, nx] (all n species).  ``bc`` names the six faces
@@ -167,6 +167,7 @@ def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "
     "dirichlet"; ``xb`` is [6, n], the composition held on each Dirichlet face
     (rows of other faces are ignored).  Returns ``x`` of the same shape at
     t = steps; with ``flux=True`` also ``J`` of shape [n, dim, nz, ny, nx]; with
+    ``grad=True`` also the local gradients of Eq. xix, same shape; with
     ``snapshots`` (ascending step counts <= steps) also the mole-fraction fields
     at those steps, shape [len(snapshots), n, nz, ny, nx].
     """
@@ -179,6 +180,7 @@ def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "
         xb = _f64(np.nan_to_num(np.asarray(xb, dtype=np.float64)).reshape(6, n))
     xo = np.zeros_like(x0)
     Jo = np.zeros((n, dim, nz, ny, nx)) if flux else None
+    Go = np.zeros((n, dim, nz, ny, nx)) if grad else None
     if snapshots is not None:
         snap = np.ascontiguousarray(np.asarray(snapshots, dtype=np.int64))
         if snap.size and (np.any(np.diff(snap) <= 0) or snap[0] < 0 or snap[-1] > steps):
@@ -186,16 +188,19 @@ def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "
         so = np.zeros((snap.size,) + x0.shape)
         rc = lib().orc_run_snap(LATTICES[lattice], n, nx, ny, nz, _p(D), RELAX[relax], _p(bcs),
                                 None if xb is None else _p(xb), _p(x0), int(steps), _p(xo), _p(Jo) if flux else None,
-                                int(snap.size), _p(snap), _p(so))
+                                _p(Go) if grad else None, int(snap.size), _p(snap), _p(so))
     else:
         so = None
         rc = lib().orc_run(LATTICES[lattice], n, nx, ny, nz, _p(D), RELAX[relax], _p(bcs),
-                           None if xb is None else _p(xb), _p(x0), int(steps), _p(xo), _p(Jo) if flux else None)
+                           None if xb is None else _p(xb), _p(x0), int(steps), _p(xo), _p(Jo) if flux else None,
+                           _p(Go) if grad else None)
     if rc != 0:
         raise RuntimeError("oracle run failed with code %d" % rc)
     out = [xo]
     if flux:
         out.append(Jo)
+    if grad:
+        out.append(Go)
     if snapshots is not None:
         out.append(so)
     return out[0] if len(out) == 1 else tuple(out)

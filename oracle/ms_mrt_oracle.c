@@ -34,10 +34,11 @@
  *      takes the kind and composition of the first wall face in axis order x, y,
  *      z; the paper does not treat corners.
  * Outputs (after the last step, at time t = steps): the mole fractions of all n
- * species and the diffusion fluxes.  The flux uses the local gradient of
- * Eq. xix, grad xi_i = -(1/c_s^2) sum_j lambda_1^{ij} sum_k c_k f_k^j (pre-
- * collision f), then the generalised Fick law J_i = -sum_j D~_ij grad xi_j
- * (Eq. 2-12, c_t = 1) and J_n = -sum_i J_i (Eq. 2-3a).
+ * species, the local mole-fraction gradients and the diffusion fluxes.  The
+ * gradient is Eq. xix, grad xi_i = -(1/c_s^2) sum_j lambda_1^{ij} sum_k c_k f_k^j
+ * (pre-collision f), with grad xi_n = -sum_i grad xi_i; the flux follows from
+ * the generalised Fick law J_i = -sum_j D~_ij grad xi_j (Eq. 2-12, c_t = 1) and
+ * J_n = -sum_i J_i (Eq. 2-3a).
  *
  * Storage here is array-of-structures, f[cell][species][k], and the lattice
  * velocity order is the one printed in Eqs. 3-7, 3-8 and 3-10.
@@ -417,7 +418,8 @@ static void write_xi(const orc_lattice* L, int n, long cells, long per, const do
  * ascending step counts snap_steps[0..n_snap) into snap_out[n_snap][n][cells]. */
 int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int relax,
                  const int* bc, const double* xb, const double* x0, long steps, double* x_out,
-                 double* J_out, int n_snap, const long* snap_steps, double* snap_out)
+                 double* J_out, double* G_out, int n_snap, const long* snap_steps,
+                 double* snap_out)
 {
     orc_lattice L;
     if (n < 2 || n > ORC_MAXN || nx < 1 || ny < 1 || nz < 1 || steps < 0) return -1;
@@ -489,8 +491,9 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
 
     if (!err) {
         write_xi(&L, n, cells, per, f, x_out);
-        for (long c = 0; c < cells && J_out; ++c) {
+        for (long c = 0; c < cells && (J_out || G_out); ++c) {
             double xi[ORC_MAXN], grad[ORC_MAXN][3], Jn[3] = {0.0, 0.0, 0.0};
+            double Gn[3] = {0.0, 0.0, 0.0};
             double L1[ORC_MAXN * ORC_MAXN], L2[ORC_MAXN * ORC_MAXN], Dt[ORC_MAXN * ORC_MAXN];
             node_xi(&L, n, &f[c * per], xi);
             if (ms_lambdas(n, xi, D, L.cs2, relax, L1, L2) || ms_Dtilde(n, xi, D, Dt)) {
@@ -507,7 +510,12 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
                         acc += L1[i * S + j] * m1;
                     }
                     grad[i][a] = -acc / L.cs2;
+                    Gn[a] -= grad[i][a];
+                    if (G_out) G_out[((long)i * L.dim + a) * cells + c] = grad[i][a];
                 }
+            if (G_out)
+                for (int a = 0; a < L.dim; ++a) G_out[((long)S * L.dim + a) * cells + c] = Gn[a];
+            if (!J_out) continue;
             /* Eq. 2-12 with c_t = 1, and Eq. 2-3a for the last species. */
             for (int i = 0; i < S; ++i)
                 for (int a = 0; a < L.dim; ++a) {
@@ -526,8 +534,9 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
 
 /*
  * Run `steps` time steps from f = f_eq(x0) (Sec. 4, initialisation) and write the
- * mole fractions x_out[n][cells] and, if J_out is not NULL, the diffusion fluxes
- * J_out[n][dim][cells] at t = steps.  Fields are [z][y][x] with x fastest.
+ * mole fractions x_out[n][cells] and, if J_out / G_out are not NULL, the
+ * diffusion fluxes J_out[n][dim][cells] and the local gradients
+ * G_out[n][dim][cells] (Eq. xix) at t = steps.  Fields are [z][y][x] with x fastest.
  * bc[6] = (x-low, x-high, y-low, y-high, z-low, z-high), each ORC_PERIODIC,
  * ORC_NOFLUX or ORC_DIRICHLET; a periodic axis must be periodic on both faces.
  * xb[6][n] holds the boundary composition of each Dirichlet face (read only
@@ -536,8 +545,8 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
  */
 int orc_run(int lat, int n, int nx, int ny, int nz, const double* D, int relax,
             const int* bc, const double* xb, const double* x0, long steps, double* x_out,
-            double* J_out)
+            double* J_out, double* G_out)
 {
-    return orc_run_snap(lat, n, nx, ny, nz, D, relax, bc, xb, x0, steps, x_out, J_out, 0, NULL,
-                        NULL);
+    return orc_run_snap(lat, n, nx, ny, nz, D, relax, bc, xb, x0, steps, x_out, J_out, G_out, 0,
+                        NULL, NULL);
 }

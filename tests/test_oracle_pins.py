@@ -367,6 +367,35 @@ def test_ternary_continuum_decay():
     np.testing.assert_allclose(amp, pred, rtol=0, atol=4e-3 * np.abs(v[:2]).max())
 
 
+@pytest.mark.parametrize("lat,axis", [("D2Q5", 0), ("D2Q9", 1), ("D3Q7", 2)])
+def test_local_gradient_is_second_order(lat, axis):
+    """Eq. xix: the gradient read from the first moments of the populations
+    equals the spectral derivative of the mole-fraction field to O(dx^2)."""
+    o = _oracle()
+    D = sy.D_from_pairs(3, {(1, 2): 0.1, (1, 3): 0.08, (2, 3): 0.02})
+    errs = []
+    for nx in (32, 64):
+        dims = [1, 1, 1]  # (nx, ny, nz)
+        dims[axis] = nx
+        dims[(axis + 1) % (3 if lat == "D3Q7" else 2)] = 2
+        k = [0, 0, 0]
+        k[axis] = 1
+        x0 = sy.small_mode([0.3, 0.3, 0.4], [1.0, -0.4, -0.6], 0.02, *dims, k=tuple(k))
+        x, G = o.run(lat, D, x0, 200, grad=True)
+        ax = 3 - axis  # array axis of the field [n, nz, ny, nx]
+        shape = [1, 1, 1, 1]
+        shape[ax] = nx
+        ik = (2j * np.pi * np.fft.fftfreq(nx)).reshape(shape)
+        dxi = np.real(np.fft.ifft(np.fft.fft(x, axis=ax) * ik, axis=ax))
+        errs.append(np.abs(G[:, axis] - dxi).max() / np.abs(dxi).max())
+        # the other components vanish for a plane wave
+        for a in range(G.shape[1]):
+            if a != axis:
+                assert np.abs(G[:, a]).max() < 1e-15
+    assert errs[1] < 3e-3
+    assert errs[0] / errs[1] > 3.8
+
+
 def test_binary_flux_is_fick():
     """J_1 = -D d(xi_1)/dx (Remark I) for a slow mode, to O(k^2)."""
     o = _oracle()
