@@ -173,6 +173,18 @@ int lbms_step(lbms_t* h, long n_steps);
 int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma);
 
 /*
+ * Local mole-fraction gradients at the current time t (Sec. 3.2, Eq. xix):
+ *   grad_sigma  [n][dim][nz][ny][nx]: grad xi_i = -(1/c_s^2) sum_j
+ *               lambda_1^{ij} sum_k c_k f_k^j of the pre-collision populations
+ *               at t (i < n-1; lattice units), and grad xi_n = -sum_i grad xi_i.
+ *               Zero at t = 0.  The scheme needs no finite differences: this is
+ *               the gradient the collision itself carries (Figs. 6-9 plot
+ *               -d(xi)/dx next to J).
+ * Host or device buffer; a host buffer synchronises the stream.
+ */
+int lbms_gradient(lbms_t* h, void* grad_sigma);
+
+/*
  * Total amount of each species, mass_out[i] = sum over nodes of xi_i, for all n
  * species (xi of Eq. 3-15, xi_n by Eq. 2-3b).  FP32 solvers add every node's
  * value as a 64-bit fixed-point number with 2^-k resolution, k = 59 - ceil(log2

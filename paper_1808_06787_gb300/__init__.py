@@ -13,9 +13,11 @@ from .lbms import (  # noqa: F401
     Solver,
     lbms_create,
     lbms_destroy,
+    lbms_gradient,
     lbms_last_error,
     lbms_mass,
     lbms_moments,
+    lbms_set_boundary,
     lbms_set_state,
     lbms_status,
     lbms_step,
@@ -24,3 +26,4 @@ from .lbms import (  # noqa: F401
     load,
 )
 from .autograd import MaxwellStefanLB, RunSpec, simulate  # noqa: F401
+from . import scenarios  # noqa: F401

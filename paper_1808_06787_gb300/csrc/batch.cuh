@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
         for (int s = 0; s <= S; ++s) xo[(size_t)s * cells + local] = xi[s];
     }
     if (!p.J_out) return;
-    T J[S + 1][DIM];
+    T J[S + 1][DIM], G[S + 1][DIM];
 #pragma unroll
     for (int s = 0; s <= S; ++s)
 #pragma unroll
@@ -210,30 +210,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
         T L1[S][S], L2[S][S];
         relaxation_matrices<S, T>(xi, iv, T(1.0 / L::cs2()), p.relax, L1, L2);
-        T m1[S][DIM];
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                T acc = T(0);
-#pragma unroll
-                for (int k = 1; k < Q; ++k) {
-                    const int c = a == 0 ? L::cx(k) : (a == 1 ? L::cy(k) : L::cz(k));
-                    if (c == 1) acc += f[s][k];
-                    if (c == -1) acc -= f[s][k];
-                }
-                m1[s][a] = acc;
-            }
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                T acc = m1[s][a];
-#pragma unroll
-                for (int j = 0; j < S; ++j) acc -= T(0.5) * L1[s][j] * m1[j][a];
-                J[s][a] = acc;
-                J[S][a] -= acc;
-            }
+        flux_and_gradient<LAT, S, T>(f, L1, J, G);
     }
     T* Jo = p.J_out + (size_t)DIM * p.field_off[id];
 #pragma unroll

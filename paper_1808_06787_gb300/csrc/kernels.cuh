@@ -194,6 +194,7 @@ struct FieldParams {
     const T* x_in;    // init: [S+1][stride]
     T* x_out;         // moments: [S+1][stride]
     T* J_out;         // moments: [S+1][dim][stride] or null
+    T* G_out;         // moments: local gradients [S+1][dim][stride] or null
     Geom g;
     uint32_t c0, c1, stride;
     int relax;
@@ -238,8 +239,9 @@ __global__ void __launch_bounds__(kBlock) k_init(FieldParams<T> p)
 }
 
 // Mole fractions at t from the stored post-collision populations (the collision
-// conserves each xi), and fluxes J = (I - Lambda_1/2) m_1 of the pre-collision
-// populations at t, gathered again from the previous buffer.
+// conserves each xi); fluxes J = (I - Lambda_1/2) m_1 and local gradients
+// grad xi = -Lambda_1 m_1 / c_s^2 (Eq. xix) of the pre-collision populations at
+// t, gathered again from the previous buffer.  Each output is optional.
 template <int LAT, int S, typename T>
 __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
 {
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
     const uint32_t i = blockIdx.x * kBlock + threadIdx.x;
     const uint32_t cell = p.c0 + i;
     if (cell >= p.c1) return;
-    {
+    if (p.x_out) {
         T f[S][Q];
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -260,12 +262,12 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
 #pragma unroll
         for (int s = 0; s <= S; ++s) p.x_out[(size_t)s * p.stride + i] = xi[s];
     }
-    if (!p.J_out) return;
-    T J[S + 1][DIM];
+    if (!p.J_out && !p.G_out) return;
+    T J[S + 1][DIM], G[S + 1][DIM];
 #pragma unroll
     for (int s = 0; s <= S; ++s)
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) J[s][a] = T(0);
+        for (int a = 0; a < DIM; ++a) J[s][a] = G[s][a] = T(0);
     if (p.fprev) {
         const Neighbourhood h = neighbourhood(p.g, cell);
         T f[S][Q];
@@ -274,35 +276,18 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
         mole_fractions<LAT, S, T>(f, xi);
         T L1[S][S], L2[S][S];
         relaxation_matrices<S, T>(xi, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
-        T m1[S][DIM];
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                T acc = T(0);
-#pragma unroll
-                for (int k = 1; k < Q; ++k) {
-                    const int c = a == 0 ? L::cx(k) : (a == 1 ? L::cy(k) : L::cz(k));
-                    if (c == 1) acc += f[s][k];
-                    if (c == -1) acc -= f[s][k];
-                }
-                m1[s][a] = acc;
-            }
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                T acc = m1[s][a];
-#pragma unroll
-                for (int j = 0; j < S; ++j) acc -= T(0.5) * L1[s][j] * m1[j][a];
-                J[s][a] = acc;
-                J[S][a] -= acc;
-            }
+        flux_and_gradient<LAT, S, T>(f, L1, J, G);
     }
+    if (p.J_out)
 #pragma unroll
-    for (int s = 0; s <= S; ++s)
+        for (int s = 0; s <= S; ++s)
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) p.J_out[((size_t)s * DIM + a) * p.stride + i] = J[s][a];
+            for (int a = 0; a < DIM; ++a) p.J_out[((size_t)s * DIM + a) * p.stride + i] = J[s][a];
+    if (p.G_out)
+#pragma unroll
+        for (int s = 0; s <= S; ++s)
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) p.G_out[((size_t)s * DIM + a) * p.stride + i] = G[s][a];
 }
 
 template <typename T>
@@ -368,6 +353,7 @@ cudaError_t launch(Op op, const KArgs& a)
     p.x_in = static_cast<const T*>(a.field_in);
     p.x_out = static_cast<T*>(a.field_x);
     p.J_out = static_cast<T*>(a.field_J);
+    p.G_out = static_cast<T*>(a.field_G);
     p.g = make_geom(a);
     p.c0 = a.c0; p.c1 = a.c1; p.stride = a.stride;
     p.relax = a.relax;

@@ -531,51 +531,71 @@ int lbms_step(lbms_t* h, long n_steps)
     return LBMS_OK;
 }
 
-int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma)
+namespace {
+
+// Mole fractions, fluxes and local gradients at the current time, each optional
+// (null: not written); device outputs in one launch, host outputs through the
+// staging area in chunks.
+int moments_impl(lbms_t* h, void* x_sigma, void* J_sigma, void* G_sigma)
 {
-    if (!h) return LBMS_EINVAL;
-    if (!x_sigma) return fail(h, LBMS_EINVAL, "x_sigma is NULL");
     h->err[0] = '\0';
     KArgs a = base_args(h, h->stream);
     a.fin = h->steps > 0 ? h->f[1 - h->cur] : nullptr;
     a.fout = h->f[h->cur];
-    const bool xdev = is_device_ptr(x_sigma);
-    const bool jdev = J_sigma ? is_device_ptr(J_sigma) : true;
+    const bool dev = (!x_sigma || is_device_ptr(x_sigma)) && (!J_sigma || is_device_ptr(J_sigma)) &&
+                     (!G_sigma || is_device_ptr(G_sigma));
     cudaError_t e;
-    if (xdev && jdev) {
+    if (dev) {
         a.field_x = x_sigma;
         a.field_J = J_sigma;
+        a.field_G = G_sigma;
         a.c0 = 0; a.c1 = h->cells; a.stride = h->cells;
         e = dispatch(h, OP_MOMENTS, a);
         return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "moments kernel");
     }
-    const int ncomp = h->n * (J_sigma ? 1 + h->dim : 1);
-    const uint32_t chunk = (uint32_t)(h->lay.staging_bytes / (ncomp * h->es));
-    char* xo = static_cast<char*>(x_sigma);
-    char* jo = static_cast<char*>(J_sigma);
+    // component planes in the staging chunk: x (n), J (n * dim), G (n * dim)
+    const int nx = x_sigma ? h->n : 0, nj = J_sigma ? h->n * h->dim : 0, ng = G_sigma ? h->n * h->dim : 0;
+    const uint32_t chunk = (uint32_t)(h->lay.staging_bytes / ((nx + nj + ng) * h->es));
+    char* outs[3] = {static_cast<char*>(x_sigma), static_cast<char*>(J_sigma), static_cast<char*>(G_sigma)};
+    const int planes[3] = {nx, nj, ng};
     for (uint32_t c0 = 0; c0 < h->cells; c0 += chunk) {
         const uint32_t c1 = c0 + chunk < h->cells ? c0 + chunk : h->cells;
-        a.field_x = h->staging;
-        a.field_J = J_sigma ? h->staging + (size_t)h->n * chunk * h->es : nullptr;
+        a.field_x = x_sigma ? h->staging : nullptr;
+        a.field_J = J_sigma ? h->staging + (size_t)nx * chunk * h->es : nullptr;
+        a.field_G = G_sigma ? h->staging + (size_t)(nx + nj) * chunk * h->es : nullptr;
         a.c0 = c0; a.c1 = c1; a.stride = chunk;
         e = dispatch(h, OP_MOMENTS, a);
         if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
         const size_t len = (size_t)(c1 - c0) * h->es;
-        for (int s = 0; s < h->n; ++s) {
-            e = cudaMemcpyAsync(xo + ((size_t)s * h->cells + c0) * h->es,
-                                h->staging + (size_t)s * chunk * h->es, len, cudaMemcpyDefault,
-                                h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (moments)");
-        }
-        for (int q = 0; J_sigma && q < h->n * h->dim; ++q) {
-            e = cudaMemcpyAsync(jo + ((size_t)q * h->cells + c0) * h->es,
-                                h->staging + ((size_t)h->n + q) * chunk * h->es, len,
-                                cudaMemcpyDefault, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (fluxes)");
+        int base = 0;
+        for (int o = 0; o < 3; ++o) {
+            for (int q = 0; outs[o] && q < planes[o]; ++q) {
+                e = cudaMemcpyAsync(outs[o] + ((size_t)q * h->cells + c0) * h->es,
+                                    h->staging + ((size_t)(base + q) * chunk) * h->es, len,
+                                    cudaMemcpyDefault, h->stream);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync (moments)");
+            }
+            base += planes[o];
         }
     }
     e = cudaStreamSynchronize(h->stream);
     return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaStreamSynchronize");
+}
+
+}  // namespace
+
+int lbms_moments(lbms_t* h, void* x_sigma, void* J_sigma)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!x_sigma) return fail(h, LBMS_EINVAL, "x_sigma is NULL");
+    return moments_impl(h, x_sigma, J_sigma, nullptr);
+}
+
+int lbms_gradient(lbms_t* h, void* grad_sigma)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!grad_sigma) return fail(h, LBMS_EINVAL, "grad_sigma is NULL");
+    return moments_impl(h, nullptr, nullptr, grad_sigma);
 }
 
 int lbms_mass(lbms_t* h, double* mass_out)

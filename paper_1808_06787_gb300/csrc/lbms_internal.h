@@ -28,6 +28,7 @@ struct KArgs {
     const void* field_in = nullptr;  // init: mole-fraction chunk [n][stride]
     void* field_x = nullptr;         // moments: mole-fraction chunk [n][stride]
     void* field_J = nullptr;         // moments: flux chunk [n][dim][stride] or null
+    void* field_G = nullptr;         // moments: local-gradient chunk [n][dim][stride] or null
     int nx = 1, ny = 1, nz = 1;
     uint32_t cells = 0;
     uint32_t c0 = 0, c1 = 0, stride = 0;  // cell range [c0, c1) and field stride (init, moments)

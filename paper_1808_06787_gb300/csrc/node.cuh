@@ -317,6 +317,49 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
     }
 }
 
+// From the pre-collision populations f at a node and its Lambda_1: the fluxes
+// J = (I - Lambda_1/2) m_1 (Eq. 2-12 with Eq. 3-26) and the local gradients
+// grad xi = -Lambda_1 m_1 / c_s^2 (Eq. xix), m_1 = sum_k c_k f_k; the last
+// species' rows close the sums (Eq. 2-3a).
+template <int LAT, int S, typename T>
+__device__ __forceinline__ void flux_and_gradient(const T (&f)[S][Lattice<LAT>::Q],
+                                                  const T (&L1)[S][S],
+                                                  T (&J)[S + 1][Lattice<LAT>::DIM],
+                                                  T (&G)[S + 1][Lattice<LAT>::DIM])
+{
+    using L = Lattice<LAT>;
+    constexpr int Q = L::Q;
+    constexpr int DIM = L::DIM;
+    T m1[S][DIM];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                const int c = a == 0 ? L::cx(k) : (a == 1 ? L::cy(k) : L::cz(k));
+                if (c == 1) acc += f[s][k];
+                if (c == -1) acc -= f[s][k];
+            }
+            m1[s][a] = acc;
+        }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) J[S][a] = G[S][a] = T(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            T lm = T(0);
+#pragma unroll
+            for (int j = 0; j < S; ++j) lm += L1[s][j] * m1[j][a];
+            J[s][a] = m1[s][a] - T(0.5) * lm;
+            J[S][a] -= J[s][a];
+            G[s][a] = -lm * T(1.0 / L::cs2());
+            G[S][a] -= G[s][a];
+        }
+}
+
 // Two-sum accumulation (Knuth): (s, c) += v with the rounding error kept in c.
 __device__ __forceinline__ void two_sum_add(double& s, double& c, double v)
 {

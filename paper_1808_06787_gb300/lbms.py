@@ -37,7 +37,7 @@ ERRORS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ERANGE", 6:
 
 EXPORTED = (
     "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_set_boundary", "lbms_step",
-    "lbms_moments",
+    "lbms_moments", "lbms_gradient",
     "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_last_error",
     "lbms_destroy",
     "lbms_batch_workspace_size", "lbms_batch_create", "lbms_batch_set_state", "lbms_batch_step",
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_step.restype = I
         L.lbms_moments.argtypes = [P, P, P]
         L.lbms_moments.restype = I
+        L.lbms_gradient.argtypes = [P, P]
+        L.lbms_gradient.restype = I
         L.lbms_mass.argtypes = [P, P]
         L.lbms_mass.restype = I
         L.lbms_mass_noalloc.argtypes = [I, I, P, I, P, P, P]
@@ -200,6 +202,10 @@ def lbms_step(h, n_steps: int) -> None:
 def lbms_moments(h, x_ptr: int, J_ptr: Optional[int]) -> None:
     _check(h, load().lbms_moments(h, ctypes.c_void_p(x_ptr),
                                   ctypes.c_void_p(J_ptr) if J_ptr else None), "lbms_moments")
+
+
+def lbms_gradient(h, g_ptr: int) -> None:
+    _check(h, load().lbms_gradient(h, ctypes.c_void_p(g_ptr)), "lbms_gradient")
 
 
 def lbms_mass(h, n_species: int) -> np.ndarray:
@@ -319,6 +325,14 @@ class Solver:
             self._field(J_out, self.flux_shape)
         lbms_moments(self._h, x_out.data_ptr(), J_out.data_ptr() if J_out is not None else None)
         return (x_out, J_out) if J_out is not None else x_out
+
+    def gradient(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Local mole-fraction gradients of Eq. xix, [n, dim, nz, ny, nx]."""
+        if out is None:
+            out = torch.empty(self.flux_shape, dtype=self.dtype, device=self.device)
+        self._field(out, self.flux_shape)
+        lbms_gradient(self._h, out.data_ptr())
+        return out
 
     def mass(self) -> np.ndarray:
         return lbms_mass(self._h, self.n)

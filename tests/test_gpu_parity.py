@@ -317,3 +317,35 @@ def test_invalid_calls_report_errors():
         s.step(-1)
     with pytest.raises(ValueError):
         s.set_state(torch.zeros((3, 1, 8, 9), device="cuda"))
+
+
+# Local gradients of Eq. xix: grad = -D~^{-1} J, so the flux tolerances scale
+# by 1 / min D_ij (0.01 for the seeded diffusivities): 1e-11 (FP64), 1e-4 (FP32).
+TOL_G = {torch.float64: 1e-11, torch.float32: 1e-4}
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("case", SMALL[:9], ids=lambda c: "%s-n%d-%dx%dx%d" % ((c[0], c[1]) + c[2]))
+def test_gradient_parity(case, dtype):
+    import oracle
+
+    from paper_1808_06787_gb300 import Solver
+
+    lattice, n, dims, bc = case
+    x0, D = _small_input(lattice, n, dims, 500 + n)
+    steps = 123
+    s = Solver(lattice, D, dims, bc=bc, dtype=dtype)
+    s.set_state(torch.from_numpy(x0).to(dtype).cuda())
+    assert float(s.gradient().abs().max()) == 0.0  # t = 0: no gradient yet
+    s.step(steps)
+    G = s.gradient().double().cpu().numpy()
+    host = torch.empty(s.flux_shape, dtype=dtype).pin_memory()
+    s.gradient(out=host)
+    _, Jo, Go = oracle.run(lattice, D, x0, steps, bc=bc, flux=True, grad=True)
+    assert np.abs(G - Go).max() <= TOL_G[dtype]
+    assert np.array_equal(host.double().numpy(), G)
+    # the species' gradients close to zero, and J = -D~ grad node by node is
+    # checked through the oracle's own flux
+    assert np.abs(G.sum(axis=0)).max() <= 10 * TOL_G[dtype]
+    x, J = s.moments(flux=True)
+    assert np.abs(J.double().cpu().numpy() - Jo).max() <= TOL_J[dtype]
