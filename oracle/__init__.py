@@ -29,7 +29,7 @@ _LIB_PATH = os.path.join(_BUILD, "libmsoracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2}
+LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4}
 RELAX = {"magic": 0, "srt": 1}
 BC = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 
@@ -93,9 +93,9 @@ def get_threads() -> int:
 
 def lattice_info(lattice: str):
     """(Q, dim, c[Q,3], w[Q], opp[Q], c_s^2) in the paper's velocity order."""
-    c = np.zeros((9, 3), dtype=np.int32)
-    w = np.zeros(9)
-    opp = np.zeros(9, dtype=np.int32)
+    c = np.zeros((15, 3), dtype=np.int32)
+    w = np.zeros(15)
+    opp = np.zeros(15, dtype=np.int32)
     Q = ctypes.c_int()
     dim = ctypes.c_int()
     cs2 = ctypes.c_double()

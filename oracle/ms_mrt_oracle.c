@@ -41,7 +41,8 @@
  * J_n = -sum_i J_i (Eq. 2-3a).
  *
  * Storage here is array-of-structures, f[cell][species][k], and the lattice
- * velocity order is the one printed in Eqs. 3-7, 3-8 and 3-10.
+ * velocity order is the one printed in Eqs. 3-5, 3-7, 3-8, 3-10 and 3-11
+ * (D1Q3, D2Q5, D2Q9, D3Q7, D3Q15).
  *
  * Parity of every function is pinned by the CPU test-suite against closed forms
  * and printed numbers of the paper (Remarks I-IV, the D12 = D13 form of Sec. 4.2,
@@ -55,10 +56,10 @@
 #include <omp.h>
 #endif
 
-#define ORC_MAXQ 9
+#define ORC_MAXQ 15
 #define ORC_MAXN 8
 
-enum { ORC_D2Q5 = 0, ORC_D2Q9 = 1, ORC_D3Q7 = 2 };
+enum { ORC_D2Q5 = 0, ORC_D2Q9 = 1, ORC_D3Q7 = 2, ORC_D3Q15 = 3, ORC_D1Q3 = 4 };
 enum { ORC_MAGIC = 0, ORC_SRT = 1 };
 enum { ORC_PERIODIC = 0, ORC_NOFLUX = 1, ORC_DIRICHLET = 2 };
 enum { GRP_CONSERVED = 0, GRP_ODD = 1, GRP_EVEN = 2 };
@@ -147,6 +148,24 @@ static int lattice_init(int lat, orc_lattice* L)
             L->c[k][0] = cx[k]; L->c[k][1] = cy[k]; L->c[k][2] = cz[k];
             L->w[k] = (k == 0) ? 1.0 / 4.0 : 1.0 / 8.0;
         }
+    } else if (lat == ORC_D3Q15) {
+        /* Eq. 3-11: w0 = 2/9, w1..6 = 1/9, w7..14 = 1/72. */
+        static const int cx[15] = {0, 1, -1, 0, 0, 0, 0, 1, 1, 1, 1, -1, -1, -1, -1};
+        static const int cy[15] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+        static const int cz[15] = {0, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1};
+        L->Q = 15; L->dim = 3;
+        for (int k = 0; k < 15; ++k) {
+            L->c[k][0] = cx[k]; L->c[k][1] = cy[k]; L->c[k][2] = cz[k];
+            L->w[k] = (k == 0) ? 2.0 / 9.0 : (k < 7 ? 1.0 / 9.0 : 1.0 / 72.0);
+        }
+    } else if (lat == ORC_D1Q3) {
+        /* Eq. 3-5: w0 = 2/3, w1 = w2 = 1/6. */
+        static const int cx[3] = {0, 1, -1};
+        L->Q = 3; L->dim = 1;
+        for (int k = 0; k < 3; ++k) {
+            L->c[k][0] = cx[k];
+            L->w[k] = (k == 0) ? 2.0 / 3.0 : 1.0 / 6.0;
+        }
     } else {
         return -1;
     }
@@ -185,7 +204,7 @@ static int lattice_init(int lat, orc_lattice* L)
             L->M[6][k] = (3.0 * c2 - 5.0) * y;
             L->M[7][k] = x * x - y * y;
             L->M[8][k] = x * y;
-        } else {
+        } else if (lat == ORC_D3Q7) {
             /* Orthogonal 7-moment basis for D3Q7. */
             L->M[0][k] = 1.0;
             L->M[1][k] = x;
@@ -194,6 +213,30 @@ static int lattice_init(int lat, orc_lattice* L)
             L->M[4][k] = 7.0 * c2 - 6.0;
             L->M[5][k] = 2.0 * x * x - y * y - z * z;
             L->M[6][k] = y * y - z * z;
+        } else if (lat == ORC_D3Q15) {
+            /* Orthogonal 15-moment basis: density, energy and its square,
+             * momenta and energy fluxes, the five stresses, and the third-order
+             * moment x y z. */
+            L->M[0][k] = 1.0;
+            L->M[1][k] = c2 - 2.0;
+            L->M[2][k] = 0.5 * (15.0 * c2 * c2 - 55.0 * c2 + 32.0);
+            L->M[3][k] = x;
+            L->M[4][k] = (5.0 * c2 - 13.0) * x;
+            L->M[5][k] = y;
+            L->M[6][k] = (5.0 * c2 - 13.0) * y;
+            L->M[7][k] = z;
+            L->M[8][k] = (5.0 * c2 - 13.0) * z;
+            L->M[9][k] = 3.0 * x * x - c2;
+            L->M[10][k] = y * y - z * z;
+            L->M[11][k] = x * y;
+            L->M[12][k] = y * z;
+            L->M[13][k] = x * z;
+            L->M[14][k] = x * y * z;
+        } else {
+            /* D1Q3: density, momentum, energy. */
+            L->M[0][k] = 1.0;
+            L->M[1][k] = x;
+            L->M[2][k] = 3.0 * x * x - 2.0;
         }
     }
     if (lat == ORC_D2Q5) {
@@ -203,8 +246,16 @@ static int lattice_init(int lat, orc_lattice* L)
         int g[9] = {GRP_CONSERVED, GRP_EVEN, GRP_EVEN, GRP_ODD, GRP_ODD,
                     GRP_ODD, GRP_ODD, GRP_EVEN, GRP_EVEN};
         memcpy(L->group, g, sizeof(g));
-    } else {
+    } else if (lat == ORC_D3Q7) {
         int g[7] = {GRP_CONSERVED, GRP_ODD, GRP_ODD, GRP_ODD, GRP_EVEN, GRP_EVEN, GRP_EVEN};
+        memcpy(L->group, g, sizeof(g));
+    } else if (lat == ORC_D3Q15) {
+        int g[15] = {GRP_CONSERVED, GRP_EVEN, GRP_EVEN, GRP_ODD, GRP_ODD, GRP_ODD, GRP_ODD,
+                     GRP_ODD, GRP_ODD, GRP_EVEN, GRP_EVEN, GRP_EVEN, GRP_EVEN, GRP_EVEN,
+                     GRP_ODD};
+        memcpy(L->group, g, sizeof(g));
+    } else {
+        int g[3] = {GRP_CONSERVED, GRP_ODD, GRP_EVEN};
         memcpy(L->group, g, sizeof(g));
     }
     /* M^{-1} by numerical inversion of the packed Q x Q matrix. */
@@ -424,7 +475,8 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
     orc_lattice L;
     if (n < 2 || n > ORC_MAXN || nx < 1 || ny < 1 || nz < 1 || steps < 0) return -1;
     if (lattice_init(lat, &L)) return -1;
-    if (L.dim == 2 && nz != 1) return -1;
+    if (L.dim < 3 && nz != 1) return -1;
+    if (L.dim == 1 && ny != 1) return -1;
     for (int a = 0; a < 6; ++a) {
         if (bc[a] < ORC_PERIODIC || bc[a] > ORC_DIRICHLET) return -1;
         if (bc[a] == ORC_DIRICHLET && !xb) return -1;

@@ -21,7 +21,7 @@ import theory as th
 
 pytestmark = pytest.mark.usefixtures("oracle_lib")
 
-LATTICES = ["D2Q5", "D2Q9", "D3Q7"]
+LATTICES = ["D2Q5", "D2Q9", "D3Q7", "D3Q15", "D1Q3"]
 
 
 def _oracle():
@@ -248,6 +248,9 @@ CASES = [
     ("D2Q9", (16, 12, 1), (1, 1, 0)),
     ("D2Q9", (20, 1, 1), (3, 0, 0)),
     ("D3Q7", (8, 6, 5), (1, 1, 2)),
+    ("D3Q15", (6, 5, 4), (1, 2, 1)),
+    ("D3Q15", (9, 1, 1), (2, 0, 0)),
+    ("D1Q3", (24, 1, 1), (3, 0, 0)),
 ]
 
 
@@ -277,7 +280,7 @@ def test_binary_mode_exact(lat, dims, k, relax):
     np.testing.assert_allclose(x[0], pred, rtol=0, atol=2e-14)
     np.testing.assert_allclose(x[1], 1.0 - pred, rtol=0, atol=2e-14)
     # flux of the pre-collision state: J = (1 - l1/2) m_1 (equals -D~ grad xi of Eq. xix)
-    dim = 3 if lat == "D3Q7" else 2
+    dim = o.lattice_info(lat)[1]
     for a in range(dim):
         Jp = (1.0 - 0.5 * l1) * th.mode_field(m1_hat[0, a], theta, shape)
         np.testing.assert_allclose(J[0, a], Jp, rtol=0, atol=2e-15)
@@ -291,8 +294,10 @@ def test_ternary_linear_response_exact(lat):
     o = _oracle()
     c, w = th.golden_lattice(lat)
     cs2 = th.cs2_of(c, w)
-    dims = {"D2Q5": (16, 6, 1), "D2Q9": (12, 8, 1), "D3Q7": (8, 4, 6)}[lat]
-    k = {"D2Q5": (1, 1, 0), "D2Q9": (1, 1, 0), "D3Q7": (1, 0, 1)}[lat]
+    dims = {"D2Q5": (16, 6, 1), "D2Q9": (12, 8, 1), "D3Q7": (8, 4, 6), "D3Q15": (6, 4, 5),
+            "D1Q3": (16, 1, 1)}[lat]
+    k = {"D2Q5": (1, 1, 0), "D2Q9": (1, 1, 0), "D3Q7": (1, 0, 1), "D3Q15": (1, 1, 1),
+         "D1Q3": (1, 0, 0)}[lat]
     nx, ny, nz = dims
     shape = (nz, ny, nx)
     D12, D13, D23 = 0.10, 0.08, 0.02
@@ -367,7 +372,8 @@ def test_ternary_continuum_decay():
     np.testing.assert_allclose(amp, pred, rtol=0, atol=4e-3 * np.abs(v[:2]).max())
 
 
-@pytest.mark.parametrize("lat,axis", [("D2Q5", 0), ("D2Q9", 1), ("D3Q7", 2)])
+@pytest.mark.parametrize("lat,axis", [("D2Q5", 0), ("D2Q9", 1), ("D3Q7", 2), ("D3Q15", 1),
+                                      ("D1Q3", 0)])
 def test_local_gradient_is_second_order(lat, axis):
     """Eq. xix: the gradient read from the first moments of the populations
     equals the spectral derivative of the mole-fraction field to O(dx^2)."""
@@ -377,7 +383,9 @@ def test_local_gradient_is_second_order(lat, axis):
     for nx in (32, 64):
         dims = [1, 1, 1]  # (nx, ny, nz)
         dims[axis] = nx
-        dims[(axis + 1) % (3 if lat == "D3Q7" else 2)] = 2
+        dim = o.lattice_info(lat)[1]
+        if dim > 1:
+            dims[(axis + 1) % dim] = 2
         k = [0, 0, 0]
         k[axis] = 1
         x0 = sy.small_mode([0.3, 0.3, 0.4], [1.0, -0.4, -0.6], 0.02, *dims, k=tuple(k))
@@ -417,13 +425,17 @@ def test_binary_flux_is_fick():
     ("D2Q9", ("periodic", "periodic", "noflux", "noflux", "periodic", "periodic")),
     ("D2Q5", ("noflux",) * 4 + ("periodic",) * 2),
     ("D3Q7", ("noflux",) * 6),
+    ("D3Q15", ("noflux", "noflux", "periodic", "periodic", "noflux", "noflux")),
+    ("D1Q3", ("noflux", "noflux") + ("periodic",) * 4),
 ])
 def test_mass_conservation_and_closure(lat, bc):
     o = _oracle()
     n = 4
     D = sy.random_D(n, seed=43)
-    if lat == "D3Q7":
+    if lat in ("D3Q7", "D3Q15"):
         x0 = sy.sin_modes(n, 9, 7, 6, amp=0.1, seed=44)
+    elif lat == "D1Q3":
+        x0 = sy.sin_modes(n, 37, 1, amp=0.1, seed=46)
     else:
         x0 = sy.sin_modes(n, 13, 11, amp=0.1, seed=45)
     x = o.run(lat, D, x0, 150, bc=bc)
@@ -431,7 +443,7 @@ def test_mass_conservation_and_closure(lat, bc):
     np.testing.assert_allclose(x.sum(axis=0), 1.0, atol=1e-14)
 
 
-@pytest.mark.parametrize("lat", ["D2Q5", "D3Q7"])
+@pytest.mark.parametrize("lat", ["D2Q5", "D3Q7", "D1Q3"])
 def test_bounce_back_equals_mirrored_periodic(lat):
     """Half-way bounce-back on [0, L) equals a periodic run of the mirrored field on
     [0, 2L) (exact for the axis-aligned lattices)."""
@@ -441,6 +453,9 @@ def test_bounce_back_equals_mirrored_periodic(lat):
     if lat == "D2Q5":
         x0 = sy.sin_modes(n, 10, 7, amp=0.1, seed=47)
         axes = (3, 2)
+    elif lat == "D1Q3":
+        x0 = sy.sin_modes(n, 17, 1, amp=0.1, seed=49)
+        axes = (3,)
     else:
         x0 = sy.sin_modes(n, 6, 5, 4, amp=0.1, seed=48)
         axes = (3, 2, 1)
@@ -464,6 +479,20 @@ def test_d2q9_bounce_back_y_uniform():
     closed = o.run("D2Q9", D, x0, 60, bc=bc)
     per = o.run("D2Q9", D, big, 60)
     np.testing.assert_allclose(closed, per[..., :12], rtol=0, atol=1e-14)
+
+
+def test_d3q15_bounce_back_yz_uniform():
+    """D3Q15 with walls in x and y/z-uniform data equals the mirrored periodic run
+    (the diagonal populations (c_x, c_y, c_z) and (c_x, -c_y, -c_z) agree by symmetry,
+    so bounce-back and mirror reflection give the same populations)."""
+    o = _oracle()
+    D = sy.D_from_pairs(3, {(1, 2): 0.1, (1, 3): 0.08, (2, 3): 0.02})
+    x0 = sy.two_bulb(10, 3, 2, width=2.0)
+    big = np.concatenate([x0, np.flip(x0, axis=3)], axis=3)
+    bc = ("noflux", "noflux") + ("periodic",) * 4
+    closed = o.run("D3Q15", D, x0, 50, bc=bc)
+    per = o.run("D3Q15", D, big, 50)
+    np.testing.assert_allclose(closed, per[..., :10], rtol=0, atol=1e-14)
 
 
 def test_closed_tube_3d_equals_1d():
