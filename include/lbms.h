@@ -46,8 +46,9 @@ extern "C" {
 
 typedef struct lbms_s lbms_t;
 
-/* Lattices of Sec. 3.1: D2Q5 (Eq. 3-7), D2Q9 (Eq. 3-8), D3Q7 (Eq. 3-10). */
-enum { LBMS_D2Q5 = 0, LBMS_D2Q9 = 1, LBMS_D3Q7 = 2 };
+/* Lattices of Sec. 3.1: D2Q5 (Eq. 3-7), D2Q9 (Eq. 3-8), D3Q7 (Eq. 3-10),
+ * D3Q15 (Eq. 3-11) and D1Q3 (Eq. 3-5).  Batched solves take the first three. */
+enum { LBMS_D2Q5 = 0, LBMS_D2Q9 = 1, LBMS_D3Q7 = 2, LBMS_D3Q15 = 3, LBMS_D1Q3 = 4 };
 
 /* Storage and arithmetic type of the populations and of all fields. */
 enum { LBMS_F32 = 0, LBMS_F64 = 1 };
@@ -99,10 +100,11 @@ size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dt
 /*
  * Create a solver handle.
  *   out        receives the handle (set to NULL on failure).
- *   lattice    LBMS_D2Q5 | LBMS_D2Q9 | LBMS_D3Q7 (Sec. 3.1).
+ *   lattice    LBMS_D2Q5 | LBMS_D2Q9 | LBMS_D3Q7 | LBMS_D3Q15 | LBMS_D1Q3
+ *              (Sec. 3.1).
  *   n_species  n, 2..8.  S = n - 1 species are evolved (Eq. 3-2, i <= n-1).
- *   grid       {nx, ny, nz}, each >= 1; nz must be 1 for 2D lattices;
- *              nx * ny * nz <= LBMS_MAX_CELLS.
+ *   grid       {nx, ny, nz}, each >= 1; nz must be 1 for 2D lattices and
+ *              ny = nz = 1 for D1Q3; nx * ny * nz <= LBMS_MAX_CELLS.
  *   D          host array of n * n binary Maxwell-Stefan diffusivities D_ij in
  *              lattice units (Eq. 2-7), row-major.  Off-diagonal entries must be
  *              finite, > 0 and symmetric (D_ij = D_ji); the diagonal is ignored.

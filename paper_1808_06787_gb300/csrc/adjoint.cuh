@@ -411,5 +411,7 @@ cudaError_t adj_dispatch_lattice(AdjOp op, int dtype, const AArgs& a)
 cudaError_t adj_dispatch_d2q5(AdjOp op, int dtype, const AArgs& a);
 cudaError_t adj_dispatch_d2q9(AdjOp op, int dtype, const AArgs& a);
 cudaError_t adj_dispatch_d3q7(AdjOp op, int dtype, const AArgs& a);
+cudaError_t adj_dispatch_d3q15(AdjOp op, int dtype, const AArgs& a);
+cudaError_t adj_dispatch_d1q3(AdjOp op, int dtype, const AArgs& a);
 
 }  // namespace lbms

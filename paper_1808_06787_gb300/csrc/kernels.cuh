@@ -133,16 +133,20 @@ __device__ __forceinline__ void write_mass_partials(const double (&xi)[S + 1], b
 // Blocks per SM the FP32 step kernels are compiled for (register budget): one
 // node per thread keeps S * Q populations and the S x S matrices in registers,
 // and enough resident warps must remain to cover HBM latency.
-template <int S, typename T>
+template <int LAT, int S, typename T>
 struct StepOccupancy {
-    static constexpr int value = sizeof(T) == 4 ? (S <= 2 ? 6 : (S == 3 ? 4 : (S == 4 ? 3 : 2))) : 1;
+    static constexpr int P = S * Lattice<LAT>::Q;  // populations held per thread
+    static constexpr int value =
+        sizeof(T) != 4 ? 1
+        : Lattice<LAT>::Q <= 9 ? (S <= 2 ? 6 : (S == 3 ? 4 : (S == 4 ? 3 : 2)))
+                               : (P <= 15 ? 4 : (P <= 30 ? 3 : 2));
 };
 
 // One time step: pull-stream (Eq. 3-13b, bounce-back/periodic faces), mole
 // fractions (Eq. 3-15), relaxation matrices (Eqs. 2-10, 3-26, 3-16), collision
 // (Eq. 3-13a with f_eq of Eq. 3-3) and store of the post-collision populations.
 template <int LAT, int S, typename T, bool MASS>
-__global__ void __launch_bounds__(kBlock, StepOccupancy<S, T>::value) k_step(StepParams<T> p)
+__global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_step(StepParams<T> p)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;

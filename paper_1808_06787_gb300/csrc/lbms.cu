@@ -23,8 +23,18 @@ constexpr int kGraphSteps = 32;                   // steps per captured graph (e
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-int lattice_q(int lat) { return lat == LBMS_D2Q5 ? 5 : lat == LBMS_D2Q9 ? 9 : lat == LBMS_D3Q7 ? 7 : 0; }
-int lattice_dim(int lat) { return lat == LBMS_D3Q7 ? 3 : 2; }
+int lattice_q(int lat)
+{
+    switch (lat) {
+        case LBMS_D2Q5: return 5;
+        case LBMS_D2Q9: return 9;
+        case LBMS_D3Q7: return 7;
+        case LBMS_D3Q15: return 15;
+        case LBMS_D1Q3: return 3;
+        default: return 0;
+    }
+}
+int lattice_dim(int lat) { return lat == LBMS_D3Q7 || lat == LBMS_D3Q15 ? 3 : (lat == LBMS_D1Q3 ? 1 : 2); }
 
 struct Layout {
     size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_bound, off_staging,
@@ -37,7 +47,8 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
     if (!Q || n < 2 || n > LBMS_MAX_SPECIES || !grid) return false;
     if (dtype != LBMS_F32 && dtype != LBMS_F64) return false;
     if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) return false;
-    if (lattice_dim(lat) == 2 && grid[2] != 1) return false;
+    if (lattice_dim(lat) < 3 && grid[2] != 1) return false;
+    if (lattice_dim(lat) == 1 && grid[1] != 1) return false;
     const double cells_d = (double)grid[0] * grid[1] * grid[2];
     if (cells_d > (double)LBMS_MAX_CELLS) return false;
     const size_t cells = (size_t)grid[0] * grid[1] * grid[2];
@@ -198,7 +209,9 @@ cudaError_t dispatch(const lbms_t* h, Op op, const KArgs& a)
     switch (h->lattice) {
         case LBMS_D2Q5: return dispatch_d2q5(op, h->dtype, a);
         case LBMS_D2Q9: return dispatch_d2q9(op, h->dtype, a);
-        default: return dispatch_d3q7(op, h->dtype, a);
+        case LBMS_D3Q7: return dispatch_d3q7(op, h->dtype, a);
+        case LBMS_D3Q15: return dispatch_d3q15(op, h->dtype, a);
+        default: return dispatch_d1q3(op, h->dtype, a);
     }
 }
 
@@ -207,7 +220,9 @@ cudaError_t adj_dispatch(const lbms_t* h, AdjOp op, const AArgs& a)
     switch (h->lattice) {
         case LBMS_D2Q5: return adj_dispatch_d2q5(op, h->dtype, a);
         case LBMS_D2Q9: return adj_dispatch_d2q9(op, h->dtype, a);
-        default: return adj_dispatch_d3q7(op, h->dtype, a);
+        case LBMS_D3Q7: return adj_dispatch_d3q7(op, h->dtype, a);
+        case LBMS_D3Q15: return adj_dispatch_d3q15(op, h->dtype, a);
+        default: return adj_dispatch_d1q3(op, h->dtype, a);
     }
 }
 

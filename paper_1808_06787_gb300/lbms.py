@@ -22,9 +22,9 @@ import torch
 
 from . import build as _build
 
-LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2}
-DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3}
-Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7}
+LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4}
+DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q15": 3, "D1Q3": 1}
+Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7, "D3Q15": 15, "D1Q3": 3}
 RELAX = {"magic": 0, "srt": 1}
 FACE = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 DTYPES = {torch.float32: 0, torch.float64: 1}

@@ -46,13 +46,13 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in p.EXPORTED, name
 
 
-@pytest.mark.parametrize("lat,q,dim", [(0, 5, 2), (1, 9, 2), (2, 7, 3)])
+@pytest.mark.parametrize("lat,q,dim", [(0, 5, 2), (1, 9, 2), (2, 7, 3), (3, 15, 3), (4, 3, 1)])
 @pytest.mark.parametrize("n", [2, 3, 8])
 @pytest.mark.parametrize("dtype,es", [(0, 4), (1, 8)])
 def test_workspace_size(lib, lat, q, dim, n, dtype, es):
     import paper_1808_06787_gb300 as p
 
-    grid = (37, 23, 11 if dim == 3 else 1)
+    grid = (37, 23 if dim > 1 else 1, 11 if dim == 3 else 1)
     cells = grid[0] * grid[1] * grid[2]
     size = p.lbms_workspace_size(lat, n, grid, dtype)
     pop = (n - 1) * q * cells * es
@@ -68,7 +68,8 @@ def test_workspace_size_rejects(lib):
     assert p.lbms_workspace_size(0, 9, (4, 4, 1), 0) == 0  # too many
     assert p.lbms_workspace_size(0, 3, (4, 4, 2), 0) == 0  # 2D lattice, nz > 1
     assert p.lbms_workspace_size(2, 3, (0, 4, 4), 0) == 0  # empty grid
-    assert p.lbms_workspace_size(3, 3, (4, 4, 4), 0) == 0  # unknown lattice
+    assert p.lbms_workspace_size(5, 3, (4, 4, 4), 0) == 0  # unknown lattice
+    assert p.lbms_workspace_size(4, 3, (4, 2, 1), 0) == 0  # 1D lattice, ny > 1
     assert p.lbms_workspace_size(2, 3, (4, 4, 4), 2) == 0  # unknown dtype
     assert p.lbms_workspace_size(2, 3, (2048, 2048, 1024), 0) == 0  # beyond 2^31 cells
 

@@ -43,6 +43,8 @@ def _one_step(s, f, step=0):
     ("D2Q9", 4, (17, 11, 1), (P, P, W, W, P, P)),
     ("D3Q7", 5, (9, 7, 6), (W, W, P, P, W, W)),
     ("D2Q9", 2, (12, 9, 1), (P,) * 6),
+    ("D3Q15", 4, (7, 6, 5), (W, W, P, P, W, W)),
+    ("D1Q3", 3, (33, 1, 1), (W, W, P, P, P, P)),
 ])
 def test_adjoint_step_is_transpose_of_step_derivative(lattice, n, dims, bc):
     from paper_1808_06787_gb300 import Solver

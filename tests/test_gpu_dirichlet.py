@@ -67,6 +67,8 @@ CASES = [
     ("D2Q9", 4, (11, 9, 1), (B, B, B, B, P, P)),
     ("D3Q7", 3, (13, 9, 7), (B, B, W, W, B, W)),
     ("D3Q7", 4, (9, 8, 10), (P, P, P, P, B, B)),
+    ("D3Q15", 3, (9, 7, 6), (B, B, W, W, B, W)),
+    ("D1Q3", 3, (40, 1, 1), (B, B, P, P, P, P)),
 ]
 
 
@@ -174,7 +176,8 @@ def test_second_order_convergence_on_the_gpu():
 
 
 @pytest.mark.parametrize("lattice,dims", [("D2Q5", (16, 3, 1)), ("D2Q9", (16, 3, 1)),
-                                          ("D3Q7", (16, 2, 2))])
+                                          ("D3Q7", (16, 2, 2)), ("D3Q15", (16, 2, 2)),
+                                          ("D1Q3", (16, 1, 1))])
 def test_linear_steady_state_and_stream_ordered_boundary_change(lattice, dims):
     from paper_1808_06787_gb300 import Solver
 
@@ -203,6 +206,8 @@ def test_linear_steady_state_and_stream_ordered_boundary_change(lattice, dims):
     ("D2Q5", 3, (21, 13, 1), (B, B, P, P, P, P)),
     ("D2Q9", 4, (17, 11, 1), (B, W, B, B, P, P)),
     ("D3Q7", 3, (9, 7, 6), (B, B, W, W, B, B)),
+    ("D3Q15", 3, (7, 6, 5), (B, B, W, W, P, P)),
+    ("D1Q3", 2, (30, 1, 1), (B, W, P, P, P, P)),
 ])
 def test_adjoint_step_with_dirichlet_faces_is_a_transpose(lattice, n, dims, bc):
     from paper_1808_06787_gb300 import Solver

@@ -73,6 +73,11 @@ SMALL = [
     ("D3Q7", 2, (5, 4, 3), (P, P, P, P, P, P)),
     ("D3Q7", 6, (1, 1, 40), (P, P, P, P, W, W)),
     ("D2Q5", 3, (1, 1, 1), (P, P, P, P, P, P)),
+    ("D3Q15", 3, (9, 7, 6), (W, W, P, P, W, W)),
+    ("D3Q15", 5, (7, 6, 5), (P, P, P, P, P, P)),
+    ("D3Q15", 2, (6, 5, 4), (W, W, W, W, W, W)),
+    ("D1Q3", 4, (53, 1, 1), (W, W, P, P, P, P)),
+    ("D1Q3", 8, (40, 1, 1), (P, P, P, P, P, P)),
 ]
 
 
@@ -325,7 +330,7 @@ TOL_G = {torch.float64: 1e-11, torch.float32: 1e-4}
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
-@pytest.mark.parametrize("case", SMALL[:9], ids=lambda c: "%s-n%d-%dx%dx%d" % ((c[0], c[1]) + c[2]))
+@pytest.mark.parametrize("case", SMALL[:9] + SMALL[11:14], ids=lambda c: "%s-n%d-%dx%dx%d" % ((c[0], c[1]) + c[2]))
 def test_gradient_parity(case, dtype):
     import oracle
 
