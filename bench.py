@@ -79,7 +79,7 @@ class Workload:
         import synthetic as sy
 
         nx, ny, nz = grid or self.grid
-        if self.key == "tube":
+        if self.key in ("tube", "tube15", "line"):
             return sy.two_bulb(nx, ny, nz, width=4.0)
         if self.key == "blobs":
             return sy.gaussian_blobs(self.n, nx, ny, seed=1003)
@@ -88,10 +88,12 @@ class Workload:
     def sample_grid(self, cells_target: int):
         """A block of the workload with about cells_target nodes (oracle timing)."""
         nx, ny, nz = self.grid
-        if self.key == "tube":  # x-slab of the closed tube: same physics per node
+        if self.key in ("tube", "tube15"):  # x-slab of the closed tube: same physics per node
             sy_ = max(1, min(ny, cells_target // nx))
             sz = max(1, min(nz, cells_target // (nx * sy_)))
             return (nx, sy_, sz)
+        if self.key == "line":
+            return (int(max(64, min(nx, cells_target))), 1, 1)
         side = int(max(8, min(nx, cells_target ** 0.5)))
         return (side, side, 1)
 
@@ -110,6 +112,18 @@ def make_workload(key: str, grid_edge: int) -> Workload:
                         "D2Q9 %d^2 five species, FP32, periodic, seeded Gaussian blobs "
                         "(sigma 32, amplitude 0.2), D_ij uniform in [0.01, 0.12]" % e,
                         "traffic_d2q9_2048sq_n5_f32.json")
+    if key == "tube15":
+        g = (grid_edge, grid_edge, grid_edge)
+        return Workload("tube15", "D3Q15", 15, g, 3, False, (W,) * 6,
+                        "D3Q15 %d^3 ternary two-bulb closed tube, FP32, D = (0.10, 0.08, 0.02), "
+                        "no-flux walls" % grid_edge,
+                        "traffic_d3q15_256cube_f32.json")
+    if key == "line":
+        nx = 1 << 26 if grid_edge == 256 else grid_edge
+        return Workload("line", "D1Q3", 3, (nx, 1, 1), 3, False, (W, W, P, P, P, P),
+                        "D1Q3 line of %d nodes, ternary two-bulb, FP32, D = (0.10, 0.08, 0.02), "
+                        "no-flux ends" % nx,
+                        "traffic_d1q3_64M_f32.json")
     e = grid_edge if grid_edge != 256 else 128
     return Workload("sine", "D2Q5", 5, (e, e, 1), 3, True, (P,) * 6,
                     "D2Q5 %d^2 ternary, FP64, periodic, seeded sine modes, "
@@ -316,12 +330,16 @@ def run_ours(args, wl: Workload):
         "vs_baseline": None,
         "dtype": "f64" if wl.f64 else "f32",
         "data": "synthetic (seeded %s; no dataset)" % {"tube": "two-bulb tanh profile",
+                                                      "tube15": "two-bulb tanh profile",
+                                                      "line": "two-bulb tanh profile",
                                                       "blobs": "Gaussian blobs",
                                                       "sine": "sine modes"}[wl.key],
         "config": {
             "workload": wl.description,
             "lattice": wl.lattice, "grid": list(wl.grid), "n_species": wl.n,
-            "evolved_species": wl.S, "bc": "no-flux all faces" if wl.key == "tube" else "periodic",
+            "evolved_species": wl.S,
+            "bc": {"tube": "no-flux all faces", "tube15": "no-flux all faces",
+                   "line": "no-flux ends"}.get(wl.key, "periodic"),
             "relax": "MRT, Lambda_2 by Eq. 3-16",
             "glups_n_counted": round(glups * wl.n / wl.S, 4),
             "l2": ("state %.2f GB per step vs 129 MB L2; no flush" % state_gb) if state_gb > 0.5
@@ -648,7 +666,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tube", "blobs", "sine", "batch", "adjoint"],
+    ap.add_argument("--workload", choices=["tube", "blobs", "sine", "tube15", "line", "batch",
+                                           "adjoint"],
                     default="tube")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the CPU baseline sample")

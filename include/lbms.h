@@ -229,7 +229,10 @@ int lbms_mass(lbms_t* h, double* mass_out);
 int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], int dtype,
                       const void* populations, double* mass_out, void* cuda_stream);
 
-/* OR of the status flags raised since lbms_set_state.  Synchronises the stream. */
+/* OR of the status flags raised since lbms_set_state.  The step kernels test
+ * the mole fractions on the last step of every lbms_step call (an unstable or
+ * corrupted state stays out of range or non-finite, so the test at the end of
+ * a call sees it); lbms_set_state tests its input.  Synchronises the stream. */
 int lbms_status(lbms_t* h, uint32_t* flags);
 
 /*

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
         T f[S][Q];
         pull<LAT, S, T>(p.fin, plane, cell, h, f, static_cast<const T*>(nullptr));
         mole_fractions<LAT, S, T>(f, xi);
-        check_range<S, T>(xi, p.status);
+        if (MASS) check_range<S, T>(xi, p.status);  // once per step call
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
         T L1[S][S], L2[S][S];
         relaxation_matrices<S, T>(xi, iv, T(1.0 / L::cs2()), p.relax, L1, L2);

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
         T f[S][Q];
         pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb);
         mole_fractions<LAT, S, T>(f, xi);
-        check_range<S, T>(xi, p.status);
+        if (MASS) check_range<S, T>(xi, p.status);  // once per lbms_step call
         T L1[S][S], L2[S][S];
         relaxation_matrices<S, T>(xi, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
         collide<LAT, S, T>(f, xi, L1, L2, mix32(step * 0x9e3779b9u) ^ (cell * 0x27d4eb2du));

@@ -28,8 +28,7 @@
 // The kernels use this second form, with the moving populations' increments
 // summed first and added to f_0 by an error-free two-sum, so the node's mass is
 // carried over exactly up to the single final rounding of f+_0.  In FP32 that
-// rounding is stochastic: the two-sum remainder decides, against a uniform
-// number hashed from the value's bits and the node, whether to round up or
+// rounding is stochastic: the two-sum remainder decides whether to round up or
 // down, against a uniform number hashed from the node, the species and the
 // step count, which makes the residual zero-mean and uncorrelated between
 // nodes and between steps.  Round-to-nearest residuals are not: identical
@@ -135,13 +134,13 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h)
     return h;
 }
 
-__device__ __forceinline__ float round_rest(float hi, float lo, uint32_t key)
+// `h` is a uniformly distributed 32-bit number.
+__device__ __forceinline__ float round_rest(float hi, float lo, uint32_t h)
 {
     // hi = RN(hi + lo) and |lo| <= half the gap to the neighbour on lo's side;
     // moving to that neighbour with probability |lo| / gap is unbiased.
     // (lo != 0 implies hi != 0; the neighbour of a finite non-zero float on the
     // side of lo is one step of its bit pattern away from or toward zero)
-    const uint32_t h = mix32(key);
     const float u = (float)(h >> 8) * 0x1p-24f;
     const int step = ((lo > 0.0f) == (hi > 0.0f)) ? 1 : -1;
     const float nb = __int_as_float(__float_as_int(hi) + step);
@@ -197,12 +196,15 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
             f[i][kb] = nb;
         }
     }
-    // rest population: f+_0 = f_0 + sum_{k != 0} (f_k - f+_k)
+    // rest population: f+_0 = f_0 + sum_{k != 0} (f_k - f+_k); one hash per
+    // node, and per species an odd multiple of it offset by a species constant
+    // (a bijection of a uniform 32-bit number, so again uniform)
+    const uint32_t hn = mix32(key);
 #pragma unroll
     for (int i = 0; i < S; ++i) {
         T hi, lo;
         two_sum(f[i][0], moved[i], hi, lo);
-        f[i][0] = round_rest(hi, lo, key + 0x165667b1u * (uint32_t)i);
+        f[i][0] = round_rest(hi, lo, (hn ^ (0x9e3779b9u * (uint32_t)(i + 1))) * 0x85ebca6bu);
     }
 }
 
