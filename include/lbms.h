@@ -248,20 +248,34 @@ int lbms_get_state(lbms_t* h, void* f_out);
 int lbms_set_state_raw(lbms_t* h, const void* f_in, long step);
 
 /*
+ * Recompute `count` forward steps between caller buffers, for checkpointed
+ * adjoints: from f_in (post-collision populations at step `step`, layout as
+ * lbms_get_state) the state after step + j + 1 is written to
+ * f_out + j * S * Q * cells elements, j = 0 .. count-1, bit for bit as
+ * lbms_step would produce it (the stochastic rounding is keyed by `step`).
+ * Device buffers only; f_out must not overlap f_in.  The handle's own state
+ * and step count are left as they were.  Stream-ordered, no mass diagnostic.
+ */
+int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_out);
+
+/*
  * Adjoint (reverse-mode derivative) of the step, for gradients of a loss L of
  * the final mole fractions with respect to the binary diffusivities D_ij and
  * the initial field.  It differentiates the model's map f+(t-1) -> f+(t)
  * (propagation Eq. 3-13b, collision Eq. 3-13a with Lambda_1 from Eq. 3-26 and
  * Lambda_2 from Eq. 3-16, f_eq of Eq. 3-3) in exact arithmetic.  Up to 5
- * species.  All buffers are device memory.  The adjoint state lambda is stored
- * in FP64 for every solver dtype (FP32 storage would lose its small per-step
- * changes coherently over a long backward sweep), with the population layout
- * (S * Q * cells doubles); f_prev, grad_x and grad_x0 have the handle's dtype.
- * The per-node Jacobian runs in the handle's dtype on the deviation of lambda
- * from its weighted mean over the directions, which the step maps to itself.
+ * species.  All buffers are device memory.  The adjoint state lambda has the
+ * population layout, S * Q * cells elements of 8 bytes each: an FP64 value for
+ * FP64 solvers and, for FP32 solvers, a pair of floats (hi, lo) whose sum is
+ * the value (about 48 significant bits).  Plain FP32 storage would lose the
+ * small per-step changes of lambda coherently over a long backward sweep.
+ * f_prev, grad_x and grad_x0 have the handle's dtype.  The per-node Jacobian
+ * runs in the handle's dtype on the deviation of lambda from its weighted mean
+ * over the directions, which the step maps to itself.
  *   lbms_adjoint_scratch_size  bytes of the gradient accumulator gacc
- *                              (FP64, per block and species pair); zero it
- *                              before the first step of a backward pass.
+ *                              (FP64, per warp of 32 nodes and species pair);
+ *                              zero it before the first step of a backward
+ *                              pass.
  *   lbms_adjoint_seed     lambda(T) from dL/dxi(T) ([n][cells], all species,
  *                         the closure species' entry included).
  *   lbms_adjoint_step     lambda(t-1) from lambda(t) (lam_in != lam_out), given

@@ -84,22 +84,18 @@ class MaxwellStefanLB(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_xT: torch.Tensor):
         s = ctx.solver
-        lam = torch.empty(s.state_shape, dtype=torch.float64, device=s.device)
+        lam = s.adjoint_state()
         lam2 = torch.empty_like(lam)
         s.adjoint_seed(grad_xT.to(s.dtype), lam)
         gacc = s.adjoint_scratch()
-        seg = [torch.empty(s.state_shape, dtype=s.dtype, device=s.device) for _ in range(ctx.K)]
+        seg = torch.empty((max(ctx.K - 1, 1),) + tuple(s.state_shape), dtype=s.dtype, device=s.device)
         for t0, ck in reversed(ctx.ckpts):
             t1 = min(t0 + ctx.K, ctx.T)
-            # recompute f+(t0) .. f+(t1 - 1) from the checkpoint
-            seg[0].copy_(ck)
-            s.set_state_raw(ck, t0)
-            for j in range(1, t1 - t0):
-                s.step(1)
-                s.get_state(seg[j])
+            # recompute f+(t0 + 1) .. f+(t1 - 1) from the checkpoint f+(t0)
+            s.recompute(ck, t0, t1 - t0 - 1, seg)
             # adjoint steps t1 .. t0 + 1 (step t reads f+(t - 1))
             for t in range(t1, t0, -1):
-                s.adjoint_step(seg[t - 1 - t0], lam, lam2, gacc)
+                s.adjoint_step(ck if t - 1 == t0 else seg[t - 2 - t0], lam, lam2, gacc)
                 lam, lam2 = lam2, lam
         grad_x0 = s.adjoint_initial(lam).to(ctx.x0_dtype)
         gD = torch.from_numpy(s.adjoint_reduce(gacc))

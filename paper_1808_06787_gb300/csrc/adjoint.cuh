@@ -204,25 +204,100 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
     }
 }
 
-// Precision.  The adjoint state lambda is stored in FP64 for every solver
-// precision: over a long backward sweep lambda shrinks by orders of magnitude
-// while each step changes it little, so FP32 storage would lose the changes
-// coherently (as FP32 storage of f lost mass in the forward).  The per-node
-// map is linear in lambda and maps a lambda that is uniform over the
-// directions, lambda_k = lbar = sum_k w_k lambda_k, to itself exactly (its
-// odd and even parts of g have zero sums), so
+// Precision.  Over a long backward sweep lambda shrinks by orders of magnitude
+// while each step changes it little, so storing it in FP32 would lose the
+// changes coherently (as FP32 storage of f lost mass in the forward).  The
+// per-node map is linear in lambda and maps a lambda that is uniform over the
+// directions, lambda_k = lbar, to itself exactly (its odd and even parts of g
+// have zero sums), so for any direction-uniform lbar
 //     mu(lambda) = lbar + mu(d),   d = lambda - lbar,
-// and only d, which is small, goes through the Jacobian; that runs in the
-// solver's precision.  The FP64 work per node is forming lbar, d and lbar + mu(d).
+// and only d, which is small, goes through the Jacobian, in the solver's
+// precision.  lambda itself is kept to about 48 bits or more: FP64 for FP64
+// solvers, and for FP32 solvers an unevaluated sum of two floats (hi, lo)
+// (Dekker's double-length representation), so that the whole per-node path
+// runs on the FP32 pipes: lbar = sum_k w_k hi_k in FP32, d = (hi - lbar) + lo,
+// and mu = lbar + mu(d) stored as its exact two-sum (hi, lo).
+template <typename T>
+struct LamIO;
+
+template <>
+struct LamIO<float> {
+    using type = float2;  // (hi, lo), lambda = hi + lo
+    static __device__ __forceinline__ void load(const float2* p, size_t i, float& hi, float& lo)
+    {
+        const float2 v = p[i];
+        hi = v.x;
+        lo = v.y;
+    }
+    static __device__ __forceinline__ void store(float2* p, size_t i, float lbar, float mud, bool neg)
+    {
+        float a, b;
+        two_sum(lbar, mud, a, b);
+        p[i] = neg ? make_float2(-a, -b) : make_float2(a, b);
+    }
+    static __device__ __forceinline__ float2 make(double v)
+    {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    }
+    static __device__ __forceinline__ double value(const float2* p, size_t i)
+    {
+        const float2 v = p[i];
+        return (double)v.x + (double)v.y;
+    }
+};
+
+template <>
+struct LamIO<double> {
+    using type = double;
+    static __device__ __forceinline__ void load(const double* p, size_t i, double& hi, double& lo)
+    {
+        hi = p[i];
+        lo = 0.0;
+    }
+    static __device__ __forceinline__ void store(double* p, size_t i, double lbar, double mud, bool neg)
+    {
+        const double v = lbar + mud;
+        p[i] = neg ? -v : v;
+    }
+    static __device__ __forceinline__ double make(double v) { return v; }
+    static __device__ __forceinline__ double value(const double* p, size_t i) { return p[i]; }
+};
+
+// Sum over a warp, all lanes taking part; lane 0 receives it.  FP32 values are
+// summed with a compensation term (two-sum at every level), FP64 plainly.
+__device__ __forceinline__ double warp_sum_to_double(float v)
+{
+    float c = 0.0f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, v, off);
+        const float oc = __shfl_down_sync(0xffffffffu, c, off);
+        float s, e;
+        two_sum(v, ov, s, e);
+        v = s;
+        c += e + oc;
+    }
+    return (double)v + (double)c;
+}
+
+__device__ __forceinline__ double warp_sum_to_double(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
 template <typename T>
 struct AdjParams {
-    const T* __restrict__ fprev;        // f+(t-1), solver precision
-    const double* __restrict__ lam_in;  // lambda(t)
-    double* __restrict__ lam_out;       // lambda(t-1)
-    double* gacc;                       // [blocks][npairs] accumulated dL/dc
+    using Lam = typename LamIO<T>::type;
+    const T* __restrict__ fprev;     // f+(t-1), solver precision
+    const Lam* __restrict__ lam_in;  // lambda(t)
+    Lam* __restrict__ lam_out;       // lambda(t-1)
+    double* gacc;                    // [warps][npairs] accumulated dL/dc
     Geom g;
     int relax;
-    const T* __restrict__ xb;           // Dirichlet face compositions [6][S]
+    const T* __restrict__ xb;        // Dirichlet face compositions [6][S]
     Coeffs<T> co;
 };
 
@@ -232,6 +307,7 @@ template <int LAT, int S, typename T>
 __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
 {
     using L = Lattice<LAT>;
+    using IO = LamIO<T>;
     constexpr int Q = L::Q;
     constexpr int NP = NPairs<S>::value;
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
@@ -241,27 +317,22 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
     for (int q = 0; q < NP; ++q) dc[q] = T(0);
     if (active) {
         const Neighbourhood h = neighbourhood(p.g, cell);
-        T f[S][Q], d[S][Q], mud[S][Q];
-        double lbar[S], mu[S][Q];
+        T f[S][Q], d[S][Q], mud[S][Q], lbar[S];
         pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            double lam[Q];
-            double acc = 0.0;
+            T hi[Q], lo[Q];
+            T acc = T(0);
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                lam[k] = p.lam_in[(size_t)(s * Q + k) * p.g.cells + cell];
-                acc += L::w(k) * lam[k];
+                IO::load(p.lam_in, (size_t)(s * Q + k) * p.g.cells + cell, hi[k], lo[k]);
+                acc += T(L::w(k)) * hi[k];
             }
             lbar[s] = acc;
 #pragma unroll
-            for (int k = 0; k < Q; ++k) d[s][k] = (T)(lam[k] - acc);
+            for (int k = 0; k < Q; ++k) d[s][k] = (hi[k] - acc) + lo[k];
         }
         adjoint_node<LAT, S, T>(f, d, p.co.invD, T(1.0 / L::cs2()), p.relax, mud, dc);
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int k = 0; k < Q; ++k) mu[s][k] = lbar[s] + (double)mud[s][k];
         // scatter through the gather's source slots; an anti-bounce-back link
         // (Dirichlet face) entered the forward map with a factor -1
 #pragma unroll
@@ -274,41 +345,31 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
             if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
             const uint32_t dst = bounce ? cell : (uint32_t)((int32_t)cell + off);
             const size_t plane = (size_t)(bounce ? opp(k) : k) * p.g.cells;
-            double sign = 1.0;
+            bool neg = false;
             if (k != 0 && h.dir) {
                 const int wf = link_wall<LAT>(k, h);
-                if (wf >= 0 && ((h.dir >> wf) & 1u)) sign = -1.0;
+                neg = wf >= 0 && ((h.dir >> wf) & 1u);
             }
 #pragma unroll
             for (int s = 0; s < S; ++s)
-                p.lam_out[(size_t)s * Q * p.g.cells + plane + dst] = sign * mu[s][k];
+                IO::store(p.lam_out, (size_t)s * Q * p.g.cells + plane + dst, lbar[s], mud[s][k], neg);
         }
     }
-    // per-block sums of dL/dc in FP64 (the contributions of different nodes and
-    // steps cancel strongly), accumulated over steps in the block's own slot
-    __shared__ double red[kBlock / 32];
+    // warp sums of dL/dc (the contributions of different nodes and steps cancel
+    // strongly), accumulated over steps in FP64 in the warp's own slot
+    const uint32_t warp = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        double v = (double)dc[q];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) red[warp] = v;
-        __syncthreads();
-        if (warp == 0) {
-            v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) p.gacc[(size_t)blockIdx.x * NP + q] += v;
-        }
-        __syncthreads();
+        const double v = warp_sum_to_double(dc[q]);
+        if ((threadIdx.x & 31) == 0) p.gacc[(size_t)warp * NP + q] += v;
     }
 }
 
 template <typename T>
 struct AdjFieldParams {
+    using Lam = typename LamIO<T>::type;
     const T* grad_x;  // seed: dL/dxi(T) [n][cells], solver precision
-    double* lam;      // seed: lambda(T) [S][Q][cells]; initial: lambda(0)
+    Lam* lam;         // seed: lambda(T) [S][Q][cells]; initial: lambda(0)
     T* grad_x0;       // initial: dL/dx0 [n][cells], solver precision
     uint32_t cells;
 };
@@ -323,7 +384,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_seed(AdjFieldParams<T> p)
     const double gn = (double)p.grad_x[(size_t)S * p.cells + cell];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const double v = (double)p.grad_x[(size_t)s * p.cells + cell] - gn;
+        const auto v = LamIO<T>::make((double)p.grad_x[(size_t)s * p.cells + cell] - gn);
 #pragma unroll
         for (int k = 0; k < Q; ++k) p.lam[(size_t)(s * Q + k) * p.cells + cell] = v;
     }
@@ -342,7 +403,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_initial(AdjFieldParams<T> p)
     for (int s = 0; s < S; ++s) {
         double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) acc += L::w(k) * p.lam[(size_t)(s * Q + k) * p.cells + cell];
+        for (int k = 0; k < Q; ++k) acc += L::w(k) * LamIO<T>::value(p.lam, (size_t)(s * Q + k) * p.cells + cell);
         p.grad_x0[(size_t)s * p.cells + cell] = (T)acc;
     }
     p.grad_x0[(size_t)S * p.cells + cell] = T(0);
@@ -368,8 +429,8 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
     if (op == AOP_STEP) {
         AdjParams<T> p;
         p.fprev = static_cast<const T*>(a.fprev);
-        p.lam_in = static_cast<const double*>(a.lam_in);
-        p.lam_out = static_cast<double*>(a.lam_out);
+        p.lam_in = static_cast<const typename AdjParams<T>::Lam*>(a.lam_in);
+        p.lam_out = static_cast<typename AdjParams<T>::Lam*>(a.lam_out);
         p.gacc = a.gacc;
         p.g = make_geom(a.k);
         p.relax = a.k.relax;
@@ -380,7 +441,7 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
     }
     AdjFieldParams<T> p;
     p.grad_x = static_cast<const T*>(a.grad_x);
-    p.lam = static_cast<double*>(a.lam);
+    p.lam = static_cast<typename AdjFieldParams<T>::Lam*>(a.lam);
     p.grad_x0 = static_cast<T*>(a.grad_x0);
     p.cells = a.k.cells;
     if (op == AOP_SEED)

@@ -132,15 +132,15 @@ struct GradScale {
     double v[16];  // 1 / D_pq^2 per pair
 };
 
-// dL/dD_pq = -(1/D_pq^2) sum over blocks of the accumulated dL/dc_pq (c = 1/D),
-// one block per pair, fixed order.
-__global__ void k_adjoint_reduce(const double* __restrict__ gacc, uint32_t blocks, int np, GradScale gs,
+// dL/dD_pq = -(1/D_pq^2) sum over the warps' slots of the accumulated dL/dc_pq
+// (c = 1/D), one block per pair, fixed order.
+__global__ void k_adjoint_reduce(const double* __restrict__ gacc, uint32_t slots, int np, GradScale gs,
                                  double* __restrict__ out)
 {
     __shared__ double2 red[kBlock / 32];
     const int q = blockIdx.x;
     double sum = 0.0, comp = 0.0;
-    for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x) two_sum_add(sum, comp, gacc[(size_t)b * np + q]);
+    for (uint32_t b = threadIdx.x; b < slots; b += blockDim.x) two_sum_add(sum, comp, gacc[(size_t)b * np + q]);
     block_reduce_pair(sum, comp, red);
     if (threadIdx.x == 0) out[q] = -(sum + comp) * gs.v[q];
 }
@@ -676,10 +676,45 @@ int lbms_set_state_raw(lbms_t* h, const void* f_in, long step)
     return LBMS_OK;
 }
 
+int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_out)
+{
+    if (!h) return LBMS_EINVAL;
+    if (!f_in || !f_out) return fail(h, LBMS_EINVAL, "f_in and f_out must not be NULL");
+    if (step < 0 || count < 0) return fail(h, LBMS_EINVAL, "step and count must not be negative");
+    if (!is_device_ptr(f_in) || !is_device_ptr(f_out))
+        return fail(h, LBMS_EINVAL, "f_in and f_out must be device memory");
+    if (h->dirichlet & ~h->xb_set)
+        return fail(h, LBMS_EINVAL, "Dirichlet face mask 0x%x has no composition set",
+                    h->dirichlet & ~h->xb_set);
+    h->err[0] = '\0';
+    if (count == 0) return LBMS_OK;
+    const size_t elems = (size_t)h->S * h->Q * h->cells;
+    // the two step-counter words carry step, step + 1, ... through the launches
+    k_set_word<<<1, 1, 0, h->stream>>>(h->clock, (uint32_t)step);
+    cudaError_t e = cudaGetLastError();
+    const char* src = static_cast<const char*>(f_in);
+    for (int j = 0; j < count && e == cudaSuccess; ++j) {
+        KArgs a = base_args(h, h->stream);
+        a.fin = src;
+        a.fout = static_cast<char*>(f_out) + (size_t)j * elems * h->es;
+        a.partials = h->partials;
+        a.clock_in = h->clock + (j & 1);
+        a.clock_out = h->clock + 1 - (j & 1);
+        e = dispatch(h, OP_STEP, a);
+        src = static_cast<const char*>(a.fout);
+    }
+    // give the handle's own step counter back to its state
+    if (e == cudaSuccess) {
+        k_set_word<<<1, 1, 0, h->stream>>>(h->clock + h->cur, (uint32_t)h->steps);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "recompute");
+}
+
 size_t lbms_adjoint_scratch_size(const lbms_t* h)
 {
     if (!h || h->S > 4) return 0;
-    return (size_t)h->blocks * (h->n * (h->n - 1) / 2) * sizeof(double);
+    return (size_t)h->blocks * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
 }
 
 int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
@@ -738,7 +773,8 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
         for (int q = p + 1; q < h->n; ++q, ++k) invD2[k] = h->invD[p][q] * h->invD[p][q];
     GradScale gs;
     for (int i = 0; i < np; ++i) gs.v[i] = invD2[i];
-    k_adjoint_reduce<<<np, kBlock, 0, h->stream>>>(static_cast<const double*>(gacc), h->blocks, np, gs, slot);
+    k_adjoint_reduce<<<np, kBlock, 0, h->stream>>>(static_cast<const double*>(gacc), h->blocks * (kBlock / 32),
+                                                   np, gs, slot);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dL_dD, slot, sizeof(double) * np, cudaMemcpyDefault, h->stream);

@@ -44,7 +44,8 @@ EXPORTED = (
     "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_schedule",
     "lbms_batch_get_schedule", "lbms_batch_tune", "lbms_batch_steps_done",
     "lbms_batch_last_error", "lbms_batch_destroy",
-    "lbms_get_state", "lbms_set_state_raw", "lbms_adjoint_scratch_size", "lbms_adjoint_seed",
+    "lbms_get_state", "lbms_set_state_raw", "lbms_recompute", "lbms_adjoint_scratch_size",
+    "lbms_adjoint_seed",
     "lbms_adjoint_step", "lbms_adjoint_initial", "lbms_adjoint_reduce",
 )
 BATCH_CANDIDATES = 7
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_get_state.restype = I
         L.lbms_set_state_raw.argtypes = [P, P, ctypes.c_long]
         L.lbms_set_state_raw.restype = I
+        L.lbms_recompute.argtypes = [P, P, ctypes.c_long, I, P]
+        L.lbms_recompute.restype = I
         L.lbms_adjoint_scratch_size.argtypes = [P]
         L.lbms_adjoint_scratch_size.restype = SZ
         L.lbms_adjoint_seed.argtypes = [P, P, P]
@@ -355,6 +358,29 @@ class Solver:
         _check(self._h, load().lbms_set_state_raw(self._h, ctypes.c_void_p(f.data_ptr()), int(step)),
                "lbms_set_state_raw")
         self._keep = f
+
+    def recompute(self, f_in: torch.Tensor, step: int, count: int, out: torch.Tensor) -> None:
+        """Forward steps step+1 .. step+count from f_in into out[0 .. count-1]
+        (bit-identical to ``step``); the handle's state is left unchanged."""
+        if out.dtype != self.dtype or out.numel() < count * int(np.prod(self.state_shape)):
+            raise ValueError("out must hold count states of the solver's dtype")
+        _check(self._h, load().lbms_recompute(self._h, ctypes.c_void_p(f_in.data_ptr()), int(step),
+                                              int(count), ctypes.c_void_p(out.data_ptr())),
+               "lbms_recompute")
+
+    def adjoint_state(self) -> torch.Tensor:
+        """An adjoint-state buffer: FP64 [n-1, Q, cells] for FP64 solvers, and
+        [n-1, Q, cells, 2] float pairs (hi, lo) for FP32 solvers."""
+        if self.dtype == torch.float64:
+            return torch.empty(self.state_shape, dtype=torch.float64, device=self.device)
+        return torch.empty(self.state_shape + (2,), dtype=torch.float32, device=self.device)
+
+    @staticmethod
+    def adjoint_value(lam: torch.Tensor) -> torch.Tensor:
+        """The adjoint state as FP64 values (sums the float pairs)."""
+        if lam.dtype == torch.float64:
+            return lam
+        return lam[..., 0].double() + lam[..., 1].double()
 
     def adjoint_scratch(self) -> torch.Tensor:
         nbytes = int(load().lbms_adjoint_scratch_size(self._h))

@@ -190,3 +190,78 @@ def test_config5_full_size_gradient_vs_finite_differences():
         dn[k] -= h
         fd = (float(((forward(up) - target) ** 2).sum()) - float(((forward(dn) - target) ** 2).sum())) / (2 * h)
         assert abs(gD[k] - fd) <= 1e-2 * abs(fd) + 1e-9, (k, gD[k], fd)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_recompute_is_bit_identical_and_leaves_the_handle_alone(dtype):
+    from paper_1808_06787_gb300 import Solver
+
+    n, dims = 3, (24, 20, 1)
+    s = Solver("D2Q5", sy.random_D(n, seed=81), dims, bc=(W, W, P, P, P, P), dtype=dtype)
+    s.set_state(torch.from_numpy(sy.sin_modes(n, *dims, amp=0.1, seed=82)).to(dtype).cuda())
+    s.step(5)
+    ck = s.get_state()
+    ref = []
+    for _ in range(7):
+        s.step(1)
+        ref.append(s.get_state())
+    out = torch.empty((7,) + tuple(s.state_shape), dtype=dtype, device="cuda")
+    s.recompute(ck, 5, 7, out)
+    for j in range(7):
+        assert torch.equal(out[j], ref[j]), j
+    # the handle continues from its own state and step count
+    s.step(3)
+    after = s.get_state()
+    s2 = Solver("D2Q5", sy.random_D(n, seed=81), dims, bc=(W, W, P, P, P, P), dtype=dtype)
+    s2.set_state_raw(ref[-1], 12)
+    s2.step(3)
+    assert torch.equal(after, s2.get_state())
+
+
+def _pack_pairs(w64):
+    hi = w64.float()
+    lo = (w64 - hi.double()).float()
+    return torch.stack([hi, lo], dim=-1).contiguous()
+
+
+def test_fp32_adjoint_state_keeps_48_bits():
+    """A lambda uniform over directions and nodes is a fixed point of the adjoint
+    step; the float-pair state reproduces it far below FP32 resolution."""
+    from paper_1808_06787_gb300 import Solver
+
+    n, dims = 3, (21, 13, 1)
+    s = Solver("D2Q5", sy.random_D(n, seed=83), dims, dtype=torch.float32)
+    s.set_state(torch.from_numpy(sy.sin_modes(n, *dims, amp=0.1, seed=84)).float().cuda())
+    s.step(4)
+    f = s.get_state()
+    c = torch.tensor([1.0 / 3.0 + 1e-9, -2.0 / 7.0], dtype=torch.float64)
+    w = c.view(2, 1, 1).expand(s.state_shape).contiguous().cuda()
+    lam = _pack_pairs(w)
+    out = s.adjoint_state()
+    s.adjoint_step(f, lam, out, s.adjoint_scratch())
+    got = s.adjoint_value(out)
+    assert float((got - w).abs().max()) <= 1e-13
+
+
+def test_fp32_adjoint_step_matches_fp64_step():
+    from paper_1808_06787_gb300 import Solver
+
+    n, dims = 3, (21, 13, 1)
+    D = sy.random_D(n, seed=85)
+    s64 = Solver("D2Q5", D, dims, bc=(W, W, P, P, P, P), dtype=torch.float64)
+    s64.set_state(torch.from_numpy(sy.sin_modes(n, *dims, amp=0.1, seed=86)).cuda())
+    s64.step(4)
+    f64 = s64.get_state()
+    s32 = Solver("D2Q5", D, dims, bc=(W, W, P, P, P, P), dtype=torch.float32)
+    g = torch.Generator(device="cpu").manual_seed(87)
+    # a smooth large part plus small deviations, as in a backward sweep
+    w = (0.5 + 1e-3 * torch.randn(s64.state_shape, generator=g, dtype=torch.float64)).cuda()
+    o64 = torch.empty_like(w)
+    ga64, ga32 = s64.adjoint_scratch(), s32.adjoint_scratch()
+    s64.adjoint_step(f64, w, o64, ga64)
+    o32 = s32.adjoint_state()
+    s32.adjoint_step(f64.float(), _pack_pairs(w), o32, ga32)
+    diff = (s32.adjoint_value(o32) - o64).abs().max()
+    # FP32 Jacobian on deviations of ~1e-3 (and FP32 populations): ~1e-9
+    assert float(diff) <= 2e-8
+    np.testing.assert_allclose(s32.adjoint_reduce(ga32), s64.adjoint_reduce(ga64), rtol=2e-3, atol=0)
