@@ -264,9 +264,10 @@ struct LamIO<double> {
     static __device__ __forceinline__ double value(const double* p, size_t i) { return p[i]; }
 };
 
-// Sum over a warp, all lanes taking part; lane 0 receives it.  FP32 values are
-// summed with a compensation term (two-sum at every level), FP64 plainly.
-__device__ __forceinline__ double warp_sum_to_double(float v)
+// Adds the sum of v over the warp (all lanes taking part) to *slot, from lane
+// 0.  FP32 values are summed with a compensation term (two-sum at every level)
+// and only lane 0 converts to FP64 (the FP64 pipes are narrow); FP64 plainly.
+__device__ __forceinline__ void warp_accumulate(float v, double* slot)
 {
     float c = 0.0f;
 #pragma unroll
@@ -278,14 +279,14 @@ __device__ __forceinline__ double warp_sum_to_double(float v)
         v = s;
         c += e + oc;
     }
-    return (double)v + (double)c;
+    if ((threadIdx.x & 31) == 0) *slot += (double)v + (double)c;
 }
 
-__device__ __forceinline__ double warp_sum_to_double(double v)
+__device__ __forceinline__ void warp_accumulate(double v, double* slot)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    return v;
+    if ((threadIdx.x & 31) == 0) *slot += v;
 }
 
 template <typename T>
@@ -303,8 +304,14 @@ struct AdjParams {
 
 // One adjoint step.  Each thread: gather f(t) as the forward did, form mu at its
 // node, and write mu back to the slots the forward gather read (P^T).
+// Blocks per SM the adjoint step is compiled for (register budget).
 template <int LAT, int S, typename T>
-__global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
+struct AdjOccupancy {
+    static constexpr int value = (sizeof(T) == 4 && S * Lattice<LAT>::Q <= 10) ? 4 : 1;
+};
+
+template <int LAT, int S, typename T>
+__global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjoint_step(AdjParams<T> p)
 {
     using L = Lattice<LAT>;
     using IO = LamIO<T>;
@@ -359,10 +366,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(AdjParams<T> p)
     // strongly), accumulated over steps in FP64 in the warp's own slot
     const uint32_t warp = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const double v = warp_sum_to_double(dc[q]);
-        if ((threadIdx.x & 31) == 0) p.gacc[(size_t)warp * NP + q] += v;
-    }
+    for (int q = 0; q < NP; ++q) warp_accumulate(dc[q], p.gacc + (size_t)warp * NP + q);
 }
 
 template <typename T>
