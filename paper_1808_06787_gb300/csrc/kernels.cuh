@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
-    const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
+    const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = cell < p.g.cells;
     const uint32_t step = *p.clock_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.clock_out = step + 1;
@@ -177,7 +177,7 @@ template <int LAT, int S, typename T>
 __global__ void __launch_bounds__(kBlock) k_mass(StepParams<T> p)
 {
     constexpr int Q = Lattice<LAT>::Q;
-    const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
+    const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = cell < p.g.cells;
     T xi[S + 1];
     if (active) {
@@ -342,13 +342,14 @@ cudaError_t launch(Op op, const KArgs& a)
         p.clock_out = a.clock_out;
         p.xb = static_cast<const T*>(a.xb);
         p.co = make_coeffs<T>(a);
-        const uint32_t blocks = node_blocks(a.cells);
+        const uint32_t tb = a.step_block;
+        const uint32_t blocks = (a.cells + tb - 1) / tb;
         if (op == OP_STEP)
-            k_step<LAT, S, T, false><<<blocks, kBlock, 0, a.stream>>>(p);
+            k_step<LAT, S, T, false><<<blocks, tb, 0, a.stream>>>(p);
         else if (op == OP_STEP_MASS)
-            k_step<LAT, S, T, true><<<blocks, kBlock, 0, a.stream>>>(p);
+            k_step<LAT, S, T, true><<<blocks, tb, 0, a.stream>>>(p);
         else
-            k_mass<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p);
+            k_mass<LAT, S, T><<<blocks, tb, 0, a.stream>>>(p);
         return cudaGetLastError();
     }
     FieldParams<T> p;

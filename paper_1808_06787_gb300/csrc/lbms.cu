@@ -58,7 +58,7 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
     L->off_f0 = 0;
     L->off_f1 = L->f_bytes;
     L->off_partials = 2 * L->f_bytes;
-    const size_t blocks = node_blocks((uint32_t)cells);
+    const size_t blocks = step_blocks((uint32_t)cells);
     L->off_mass = L->off_partials + align_up(blocks * n * sizeof(double2));
     L->off_status = L->off_mass + align_up(LBMS_MAX_SPECIES * sizeof(double));
     L->off_bound = L->off_status + kAlign;
@@ -160,7 +160,8 @@ int fixed_shift_for(uint32_t cells)
 struct lbms_s {
     int lattice = 0, n = 0, S = 0, Q = 0, dim = 0, dtype = 0, relax = 0;
     int nx = 1, ny = 1, nz = 1;
-    uint32_t cells = 0, blocks = 0;
+    uint32_t cells = 0, blocks = 0;  // blocks: of the step and mass kernels (mass partial slots)
+    uint32_t step_block = 256;        // their threads per block
     uint32_t noflux = 0;
     uint32_t dirichlet = 0;  // Dirichlet faces
     uint32_t xb_set = 0;     // Dirichlet faces whose composition has been set
@@ -231,6 +232,7 @@ KArgs base_args(const lbms_t* h, cudaStream_t st)
     KArgs a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
     a.cells = h->cells;
+    a.step_block = h->step_block;
     a.noflux = h->noflux;
     a.dirichlet = h->dirichlet;
     a.xb = h->xb;
@@ -389,7 +391,8 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->relax = relax;
     h->nx = grid[0]; h->ny = grid[1]; h->nz = grid[2];
     h->cells = (uint32_t)((size_t)grid[0] * grid[1] * grid[2]);
-    h->blocks = node_blocks(h->cells);
+    h->blocks = step_blocks(h->cells);
+    h->step_block = step_block_for(h->cells);
     h->noflux = noflux;
     h->dirichlet = dirichlet;
     h->es = dtype == LBMS_F64 ? 8 : 4;
@@ -714,7 +717,7 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
 size_t lbms_adjoint_scratch_size(const lbms_t* h)
 {
     if (!h || h->S > 4) return 0;
-    return (size_t)h->blocks * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
+    return (size_t)node_blocks(h->cells) * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
 }
 
 int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
@@ -773,7 +776,7 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
         for (int q = p + 1; q < h->n; ++q, ++k) invD2[k] = h->invD[p][q] * h->invD[p][q];
     GradScale gs;
     for (int i = 0; i < np; ++i) gs.v[i] = invD2[i];
-    k_adjoint_reduce<<<np, kBlock, 0, h->stream>>>(static_cast<const double*>(gacc), h->blocks * (kBlock / 32),
+    k_adjoint_reduce<<<np, kBlock, 0, h->stream>>>(static_cast<const double*>(gacc), node_blocks(h->cells) * (kBlock / 32),
                                                    np, gs, slot);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)

@@ -32,6 +32,7 @@ struct KArgs {
     int nx = 1, ny = 1, nz = 1;
     uint32_t cells = 0;
     uint32_t c0 = 0, c1 = 0, stride = 0;  // cell range [c0, c1) and field stride (init, moments)
+    uint32_t step_block = kBlock;         // threads per block of the step and mass kernels
     uint32_t noflux = 0;                  // bit f set: face f is no-flux (x-, x+, y-, y+, z-, z+)
     uint32_t dirichlet = 0;               // bit f set: face f is Dirichlet (fixed composition)
     const void* xb = nullptr;             // Dirichlet compositions [6][S] in the solver's dtype
@@ -56,6 +57,18 @@ cudaError_t dispatch_d1q3(Op op, int dtype, const KArgs& a);
 
 // Number of blocks a node kernel over `cells` nodes is launched with.
 inline uint32_t node_blocks(uint32_t cells) { return (cells + kBlock - 1) / kBlock; }
+
+// Threads per block of a solver's step and mass kernels: grids too small to give
+// every one of the 152 SMs two blocks of kBlock threads run blocks of 64, so that
+// the per-node work (FP64 in particular, whose pipes are narrow on GB300) is
+// spread over all SMs instead of a few.
+constexpr uint32_t kSmallBlock = 64;
+inline uint32_t step_block_for(uint32_t cells) { return cells < 2u * 152u * kBlock ? kSmallBlock : kBlock; }
+inline uint32_t step_blocks(uint32_t cells)
+{
+    const uint32_t tb = step_block_for(cells);
+    return (cells + tb - 1) / tb;
+}
 
 // Helpers of the host runtime shared with lbms_mass_noalloc (mass_noalloc.cu):
 // fraction bits of the FP32 fixed-point mass partials for a grid, the final
