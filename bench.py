@@ -25,6 +25,7 @@ sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -39,9 +40,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS (species-node updates/s) and % of HBM roofline"
-KERNEL_SOURCES = ["paper_1808_06787_gb300/csrc/kernels.cuh",
-                  "paper_1808_06787_gb300/csrc/node.cuh",
-                  "paper_1808_06787_gb300/csrc/lattice.cuh"]
+KERNEL_SOURCES = sorted(
+    os.path.relpath(p_, os.path.dirname(os.path.abspath(__file__)))
+    for p_ in glob.glob(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                     "paper_1808_06787_gb300", "csrc", "*.cuh")))
 
 
 @dataclass
@@ -139,17 +141,22 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(wl: Workload):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    or None when the kernel sources changed since it was taken."""
+def recorded_traffic(fname: str, grid):
+    """DRAM bytes per launch of a kernel from its committed ncu record, or None
+    when the kernel sources changed since it was taken or the size differs."""
     try:
-        with open(os.path.join(ROOT, "profiles", wl.traffic_file)) as fh:
+        with open(os.path.join(ROOT, "profiles", fname)) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_hash") != kernel_hash() or tuple(rec.get("grid", ())) != tuple(wl.grid):
+    if rec.get("kernel_hash") != kernel_hash() or list(rec.get("grid", ())) != list(grid):
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def measured_traffic(wl: Workload):
+    """DRAM bytes per launch of the workload's step kernel (see recorded_traffic)."""
+    return recorded_traffic(wl.traffic_file, wl.grid)
 
 
 def hbm_peak():
@@ -402,7 +409,12 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = BatchSolver("D2Q5", Ds, grids, bcs=bcs, dtype=torch.float32, stream=stream)
-        chosen, tune_ms = b.tune(trial_steps=16)
+        if args.batch_schedule < 0:
+            chosen, tune_ms = b.tune(trial_steps=16)
+        else:
+            b.set_schedule(args.batch_schedule)
+            chosen, tune_ms = args.batch_schedule, []
+        launches_per_step = b.launches_per_step()
         x0_host = torch.empty(int(b.offsets[-1]), dtype=torch.float32).pin_memory()
         for i in range(count):
             x0_host[int(b.offsets[i]):int(b.offsets[i + 1])] = torch.from_numpy(
@@ -476,7 +488,8 @@ def run_batch(args):
             "peak": peak,
             "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": None,
+            "traffic": recorded_traffic("traffic_batch_d2q5_4096_f32.json", [count]) if chosen == 0
+            else None,
             "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": bytes_per_step,
             "note": "algorithmic bytes of a streamed step; L2-blocked schedules move less",
@@ -487,7 +500,9 @@ def run_batch(args):
             "h2d_bytes_per_step": round(x0_host.numel() * 4 / args.steps, 1),
             "d2h_bytes_per_step": round((x0_host.numel() * 4 + 8 * 3 * count) / args.steps, 1),
         },
-        "gpu_launches": None,
+        "cpu_baseline": None if (args.no_cpu_baseline or world > 1)
+        else cpu_baseline_batch(grids, Ds, bcs, 1004 + rank, budget_s=args.cpu_budget),
+        "gpu_launches": args.steps * launches_per_step + 1,
         "clocks": clocks,
         "status_flags": flags,
         "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
@@ -539,6 +554,7 @@ def run_adjoint(args):
     dp = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
     xg = x0.clone().requires_grad_(True)
     spec = RunSpec("D2Q5", (n, n, 1), steps)
+    spec.stats["adjoint_events"] = []
     xT = simulate(xg, dp, spec)
     loss = ((xT.double() - target) ** 2).sum()
     ev[2].record()
@@ -549,6 +565,24 @@ def run_adjoint(args):
     t_fwd = ev[0].elapsed_time(ev[1])
     t_ckpt = ev[1].elapsed_time(ev[2])
     t_bwd = ev[2].elapsed_time(ev[3])
+    # the dominant kernel: the adjoint step, timed over the backward's own loops
+    adj = spec.stats["adjoint_events"]
+    adj_ms = sum(a.elapsed_time(b) for a, b, _ in adj) / sum(c for _, _, c in adj)
+    adj_bytes = float(n * n) * 2 * 5 * (4 + 8 + 8)  # f+ (FP32) read, lambda (8 B) read and written
+    peak, peak_kind = hbm_peak()
+    launches = spec.stats.get("launches")
+    # end to end through the public API: pinned host x0 in, gradients back to the host
+    x0_host = x0.cpu().pin_memory()
+    g_host = torch.empty(x0.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xd = x0_host.cuda(non_blocking=True).requires_grad_(True)
+    dpe = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
+    le = ((simulate(xd, dpe, RunSpec("D2Q5", (n, n, 1), steps)).double() - target) ** 2).sum()
+    le.backward()
+    g_host.copy_(xd.grad, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
     out = {
         "metric": "adjoint/fwd cost (gradient wrt D_ij and x0 over plain forward)",
         "value": round((t_ckpt + t_bwd) / t_fwd, 3),
@@ -560,7 +594,7 @@ def run_adjoint(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 forward, f64 adjoint state",
+        "dtype": "f32 forward, float-pair (about 48-bit) adjoint state",
         "data": "synthetic (seeded sine modes; target from D* = (0.09, 0.07, 0.02))",
         "config": {
             "workload": "adjoint: ternary D2Q5 %d^2 FP32, %d steps, L2 misfit, gradients wrt 3 "
@@ -573,9 +607,26 @@ def run_adjoint(args):
             "dL_dD": [float(v) for v in dp.grad.numpy()],
             "glups_forward": round(2.0 * n * n * steps / (t_fwd * 1e-3) / 1e9, 3),
         },
-        "roofline": None,
-        "e2e": None,
-        "gpu_launches": None,
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "k_adjoint_step<D2Q5, 2, float>",
+            "achieved": round(adj_bytes / (adj_ms * 1e-3) / 1e9, 1),
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": round(adj_bytes / (adj_ms * 1e-3) / 1e9 / peak, 4),
+            "traffic": recorded_traffic("traffic_adjoint_d2q5_512sq_f32.json", [n, n]),
+            "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": adj_bytes,
+            "avg_launch_us": round(adj_ms * 1e3, 3),
+            "note": "the 2 x 21 MB adjoint state is largely L2-resident at this size",
+        },
+        "e2e": {
+            "value": round(e2e_ms / t_fwd, 3),
+            "unit": "x forward",
+            "h2d_bytes_per_step": round(x0_host.numel() * 4 / steps, 1),
+            "d2h_bytes_per_step": round((g_host.numel() * 4 + 3 * 8) / steps, 1),
+        },
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(out))
@@ -602,7 +653,7 @@ def cpu_baseline(wl: Workload, budget_s: float = 20.0):
     rate = g1[0] * g1[1] * g1[2] / dt1  # node updates per second
     if rate * budget_s >= wl.cells:
         cells = wl.cells
-        steps = int(max(1, min(200, rate * budget_s / wl.cells)))
+        steps = int(max(1, min(20000, rate * budget_s / wl.cells)))
     else:
         cells, steps = int(max(64, rate * budget_s)), 1
     dt, g = _oracle_sample_run(wl, cells, steps)
@@ -614,6 +665,38 @@ def cpu_baseline(wl: Workload, budget_s: float = 20.0):
         "kind": "oracle",
         "sample": "%d step(s) on a %dx%dx%d block of the workload (FP64 oracle, OpenMP), %.1f s"
                   % (steps, g[0], g[1], g[2], dt),
+    }
+
+
+def cpu_baseline_batch(grids, Ds, bcs, seed: int, budget_s: float = 20.0):
+    """The oracle on the first instances of the batch, converted to solves/s
+    (5000-step solves of the batch's mean instance size)."""
+    import oracle
+
+    import synthetic as sy
+
+    oracle.build()
+    k = min(8, len(grids))
+    fields = [sy.batch_field(i, int(grids[i][0]), seed=seed) for i in range(k)]
+
+    def run(steps):
+        t0 = time.perf_counter()
+        for i in range(k):
+            oracle.run("D2Q5", Ds[i], fields[i], steps, bc=bcs[i])
+        return time.perf_counter() - t0
+
+    probe = run(1)
+    steps = int(max(1, min(5000, budget_s / max(probe, 1e-6))))
+    dt = run(steps)
+    nodes = sum(int(grids[i][0]) * int(grids[i][1]) for i in range(k))
+    rate = nodes * steps / dt  # node updates per second
+    mean_nodes = float(sum(int(g[0]) * int(g[1]) for g in grids)) / len(grids)
+    return {
+        "value": round(rate / (mean_nodes * BATCH_SOLVE_STEPS), 4),
+        "unit": "solves/s",
+        "cores": oracle.get_threads(),
+        "kind": "oracle",
+        "sample": "instances 0..%d (%d nodes), %d steps each, FP64 oracle, %.1f s" % (k - 1, nodes, steps, dt),
     }
 
 
@@ -673,6 +756,8 @@ def main():
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--batch-schedule", type=int, default=-1,
+                    help="batched workload: fixed step schedule (0..6) instead of the tuner's")
     ap.add_argument("--grid", type=int, default=256,
                     help="grid edge (256 selects each workload's own size)")
     args = ap.parse_args()

@@ -272,8 +272,9 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
  * f_prev, grad_x and grad_x0 have the handle's dtype.  The per-node Jacobian
  * runs in the handle's dtype on the deviation of lambda from its weighted mean
  * over the directions, which the step maps to itself.
- *   lbms_adjoint_scratch_size  bytes of the gradient accumulator gacc
- *                              (FP64, per warp of 32 nodes and species pair);
+ *   lbms_adjoint_scratch_size  bytes of the gradient accumulator gacc (8
+ *                              bytes per warp of 32 nodes and species pair: an
+ *                              FP64 value, or a float pair for FP32 solvers);
  *                              zero it before the first step of a backward
  *                              pass.
  *   lbms_adjoint_seed     lambda(T) from dL/dxi(T) ([n][cells], all species,
@@ -379,6 +380,12 @@ int lbms_batch_status(lbms_batch_t* b, uint32_t* flags);
  */
 int lbms_batch_set_schedule(lbms_batch_t* b, int candidate);
 int lbms_batch_get_schedule(const lbms_batch_t* b);
+
+/* Kernel launches one step takes under the current schedule (1 for the
+ * streamed schedule, the number of instance groups otherwise); a call of
+ * lbms_batch_step(n) launches n times this many step kernels and one mass
+ * reduction.  -1 for a NULL handle. */
+int lbms_batch_launches_per_step(const lbms_batch_t* b);
 
 /*
  * Schedule tuner: times every candidate over trial_steps steps (after one

@@ -65,12 +65,15 @@ class MaxwellStefanLB(torch.autograd.Function):
         K = max(1, int(math.ceil(math.sqrt(T))))
         ckpts = []
         t = 0
+        launches = 1  # set_state
         while t < T:
             ckpts.append((t, solver.get_state()))
             m = min(K, T - t)
             solver.step(m)
+            launches += m + 1  # m step kernels and the mass reduction
             t += m
         xT = solver.moments()
+        spec.stats["launches"] = launches + 1
         ctx.solver = solver
         ctx.x0_dtype = x0.dtype
         ctx.ckpts = ckpts
@@ -89,16 +92,29 @@ class MaxwellStefanLB(torch.autograd.Function):
         s.adjoint_seed(grad_xT.to(s.dtype), lam)
         gacc = s.adjoint_scratch()
         seg = torch.empty((max(ctx.K - 1, 1),) + tuple(s.state_shape), dtype=s.dtype, device=s.device)
+        # optional timing of the adjoint-step loops (CUDA events on the solver's stream)
+        events = ctx.spec.stats.get("adjoint_events")
+        launches = 1  # seed
         for t0, ck in reversed(ctx.ckpts):
             t1 = min(t0 + ctx.K, ctx.T)
             # recompute f+(t0 + 1) .. f+(t1 - 1) from the checkpoint f+(t0)
             s.recompute(ck, t0, t1 - t0 - 1, seg)
+            launches += (t1 - t0 - 1) + 2 if t1 - t0 > 1 else 0
             # adjoint steps t1 .. t0 + 1 (step t reads f+(t - 1))
+            if events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(s.stream)
             for t in range(t1, t0, -1):
                 s.adjoint_step(ck if t - 1 == t0 else seg[t - 2 - t0], lam, lam2, gacc)
                 lam, lam2 = lam2, lam
+            launches += t1 - t0
+            if events is not None:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(s.stream)
+                events.append((e0, e1, t1 - t0))
         grad_x0 = s.adjoint_initial(lam).to(ctx.x0_dtype)
         gD = torch.from_numpy(s.adjoint_reduce(gacc))
+        ctx.spec.stats["launches"] = ctx.spec.stats.get("launches", 0) + launches + 2
         return grad_x0, gD, None
 
 

@@ -264,9 +264,11 @@ struct LamIO<double> {
     static __device__ __forceinline__ double value(const double* p, size_t i) { return p[i]; }
 };
 
-// Adds the sum of v over the warp (all lanes taking part) to *slot, from lane
-// 0.  FP32 values are summed with a compensation term (two-sum at every level)
-// and only lane 0 converts to FP64 (the FP64 pipes are narrow); FP64 plainly.
+// Adds the sum of v over the warp (all lanes taking part) to the warp's
+// accumulator slot, from lane 0.  FP32 solvers keep the slot as a float pair
+// (hi, lo) and sum with two-sums, on the FP32 pipes only: on GB300 an FP64
+// instruction occupies the narrow FP64 pipe for a whole warp even with one
+// active lane.  FP64 solvers keep a double.
 __device__ __forceinline__ void warp_accumulate(float v, double* slot)
 {
     float c = 0.0f;
@@ -279,7 +281,15 @@ __device__ __forceinline__ void warp_accumulate(float v, double* slot)
         v = s;
         c += e + oc;
     }
-    if ((threadIdx.x & 31) == 0) *slot += (double)v + (double)c;
+    if ((threadIdx.x & 31) == 0) {
+        float2* acc = reinterpret_cast<float2*>(slot);
+        const float2 a = *acc;
+        float s, e;
+        two_sum(a.x, v, s, e);
+        e += a.y + c;
+        const float hi = s + e;  // |e| is below an ulp of s: renormalise
+        *acc = make_float2(hi, e - (hi - s));
+    }
 }
 
 __device__ __forceinline__ void warp_accumulate(double v, double* slot)
@@ -295,7 +305,7 @@ struct AdjParams {
     const T* __restrict__ fprev;     // f+(t-1), solver precision
     const Lam* __restrict__ lam_in;  // lambda(t)
     Lam* __restrict__ lam_out;       // lambda(t-1)
-    double* gacc;                    // [warps][npairs] accumulated dL/dc
+    double* gacc;                    // [warps][npairs] accumulated dL/dc (float pairs for FP32)
     Geom g;
     int relax;
     const T* __restrict__ xb;        // Dirichlet face compositions [6][S]
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
 #pragma unroll
     for (int q = 0; q < NP; ++q) dc[q] = T(0);
     if (active) {
-        const Neighbourhood h = neighbourhood(p.g, cell);
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
         T f[S][Q], d[S][Q], mud[S][Q], lbar[S];
         pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
 #pragma unroll

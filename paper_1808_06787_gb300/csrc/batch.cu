@@ -648,6 +648,12 @@ int lbms_batch_set_schedule(lbms_batch_t* b, int candidate)
 
 int lbms_batch_get_schedule(const lbms_batch_t* b) { return b ? b->schedule : -1; }
 
+int lbms_batch_launches_per_step(const lbms_batch_t* b)
+{
+    if (!b) return -1;
+    return b->schedule == 0 ? 1 : (int)b->groups.size();
+}
+
 int lbms_batch_tune(lbms_batch_t* b, int trial_steps, double* ms_per_step, int* chosen)
 {
     if (!b) return LBMS_EINVAL;

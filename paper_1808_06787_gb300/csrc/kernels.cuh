@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.clock_out = step + 1;
     T xi[S + 1];
     if (active) {
-        const Neighbourhood h = neighbourhood(p.g, cell);
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
         T f[S][Q];
         pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb);
         mole_fractions<LAT, S, T>(f, xi);
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
 #pragma unroll
         for (int a = 0; a < DIM; ++a) J[s][a] = G[s][a] = T(0);
     if (p.fprev) {
-        const Neighbourhood h = neighbourhood(p.g, cell);
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
         T f[S][Q];
         pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
         T xi[S + 1];

@@ -134,13 +134,21 @@ struct GradScale {
 
 // dL/dD_pq = -(1/D_pq^2) sum over the warps' slots of the accumulated dL/dc_pq
 // (c = 1/D), one block per pair, fixed order.
-__global__ void k_adjoint_reduce(const double* __restrict__ gacc, uint32_t slots, int np, GradScale gs,
-                                 double* __restrict__ out)
+__global__ void k_adjoint_reduce(const double* __restrict__ gacc, uint32_t slots, int np, int pairs_f32,
+                                 GradScale gs, double* __restrict__ out)
 {
     __shared__ double2 red[kBlock / 32];
     const int q = blockIdx.x;
     double sum = 0.0, comp = 0.0;
-    for (uint32_t b = threadIdx.x; b < slots; b += blockDim.x) two_sum_add(sum, comp, gacc[(size_t)b * np + q]);
+    for (uint32_t b = threadIdx.x; b < slots; b += blockDim.x) {
+        if (pairs_f32) {  // FP32 solvers: (hi, lo) float pairs
+            const float2 v = reinterpret_cast<const float2*>(gacc)[(size_t)b * np + q];
+            two_sum_add(sum, comp, (double)v.x);
+            two_sum_add(sum, comp, (double)v.y);
+        } else {
+            two_sum_add(sum, comp, gacc[(size_t)b * np + q]);
+        }
+    }
     block_reduce_pair(sum, comp, red);
     if (threadIdx.x == 0) out[q] = -(sum + comp) * gs.v[q];
 }
@@ -777,7 +785,7 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
     GradScale gs;
     for (int i = 0; i < np; ++i) gs.v[i] = invD2[i];
     k_adjoint_reduce<<<np, kBlock, 0, h->stream>>>(static_cast<const double*>(gacc), node_blocks(h->cells) * (kBlock / 32),
-                                                   np, gs, slot);
+                                                   np, h->dtype == LBMS_F32 ? 1 : 0, gs, slot);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dL_dD, slot, sizeof(double) * np, cudaMemcpyDefault, h->stream);

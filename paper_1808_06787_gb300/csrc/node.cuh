@@ -235,12 +235,22 @@ struct Neighbourhood {
     uint32_t dir;  // the Dirichlet faces this node lies on (bits as Geom::noflux)
 };
 
+// DIM is the lattice's dimension: a 2D grid has nz = 1 and a 1D grid ny = nz = 1,
+// so those coordinates need no division.
+template <int DIM>
 __device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t cell)
 {
-    const uint32_t row = g.dnx.div(cell);
-    const int x = (int)(cell - row * (uint32_t)g.nx);
-    const int z = (int)g.dny.div(row);
-    const int y = (int)(row - (uint32_t)z * (uint32_t)g.ny);
+    uint32_t row = 0;
+    int x = (int)cell, y = 0, z = 0;
+    if (DIM > 1) {
+        row = g.dnx.div(cell);
+        x = (int)(cell - row * (uint32_t)g.nx);
+        y = (int)row;
+    }
+    if (DIM > 2) {
+        z = (int)g.dny.div(row);
+        y = (int)(row - (uint32_t)z * (uint32_t)g.ny);
+    }
     Neighbourhood h;
     const bool xlo = x == 0, xhi = x == g.nx - 1;
     const bool ylo = y == 0, yhi = y == g.ny - 1;

@@ -42,7 +42,8 @@ EXPORTED = (
     "lbms_destroy",
     "lbms_batch_workspace_size", "lbms_batch_create", "lbms_batch_set_state", "lbms_batch_step",
     "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_schedule",
-    "lbms_batch_get_schedule", "lbms_batch_tune", "lbms_batch_steps_done",
+    "lbms_batch_get_schedule", "lbms_batch_launches_per_step", "lbms_batch_tune",
+    "lbms_batch_steps_done",
     "lbms_batch_last_error", "lbms_batch_destroy",
     "lbms_get_state", "lbms_set_state_raw", "lbms_recompute", "lbms_adjoint_scratch_size",
     "lbms_adjoint_seed",
@@ -138,6 +139,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_batch_set_schedule.restype = I
         L.lbms_batch_get_schedule.argtypes = [P]
         L.lbms_batch_get_schedule.restype = I
+        L.lbms_batch_launches_per_step.argtypes = [P]
+        L.lbms_batch_launches_per_step.restype = I
         L.lbms_batch_tune.argtypes = [P, I, P, P]
         L.lbms_batch_tune.restype = I
         L.lbms_batch_steps_done.argtypes = [P]
@@ -560,6 +563,10 @@ class BatchSolver:
     @property
     def schedule(self) -> int:
         return int(load().lbms_batch_get_schedule(self._h))
+
+    def launches_per_step(self) -> int:
+        """Step-kernel launches per step under the current schedule."""
+        return int(load().lbms_batch_launches_per_step(self._h))
 
     def tune(self, trial_steps: int = 32):
         """Time every step schedule and keep the fastest (advances the state: call
