@@ -298,6 +298,12 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD);
 /* Number of steps taken since lbms_set_state, or -1 for a NULL handle. */
 long lbms_steps_done(const lbms_t* h);
 
+/* Device address, inside the caller's workspace, of the buffer that holds the
+ * current post-collision populations (layout as lbms_get_state).  It changes
+ * with every step (the two buffers alternate) and after lbms_set_state_raw;
+ * NULL for a NULL handle. */
+const void* lbms_populations(const lbms_t* h);
+
 /* Message of the last failed call on this handle ("" if none).  With h == NULL,
  * the message of the last failed lbms_create on this thread. */
 const char* lbms_last_error(const lbms_t* h);

@@ -71,14 +71,20 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
 
 thread_local char g_create_error[256] = "";
 
-// Final fixed-order reduction of the per-block mass partials, one block per
-// species.  FP32 solvers: exact int64 fixed-point sums scaled by 2^-shift.
-__global__ void k_mass_finalize_fixed(const long long* __restrict__ partials, uint32_t blocks, int n,
-                                      int shift, double* __restrict__ out)
+// Final fixed-order reduction of the per-block mass partials, one block of
+// kFinalize threads per species (many loads in flight: the partials of a large
+// grid number tens of thousands).  FP32 solvers: exact int64 fixed-point sums
+// scaled by 2^-shift.
+constexpr int kFinalize = 1024;
+
+__global__ void __launch_bounds__(kFinalize) k_mass_finalize_fixed(const long long* __restrict__ partials,
+                                                                   uint32_t blocks, int n, int shift,
+                                                                   double* __restrict__ out)
 {
-    __shared__ long long red[kBlock / 32];
+    __shared__ long long red[kFinalize / 32];
     const int s = blockIdx.x;
     long long acc = 0;
+#pragma unroll 8
     for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x) acc += partials[(size_t)b * n + s];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -94,12 +100,14 @@ __global__ void k_mass_finalize_fixed(const long long* __restrict__ partials, ui
 }
 
 // FP64 solvers: two-sum pairs merged in a fixed order.
-__global__ void k_mass_finalize_pairs(const double2* __restrict__ partials, uint32_t blocks, int n,
-                                      double* __restrict__ out)
+__global__ void __launch_bounds__(kFinalize) k_mass_finalize_pairs(const double2* __restrict__ partials,
+                                                                   uint32_t blocks, int n,
+                                                                   double* __restrict__ out)
 {
-    __shared__ double2 red[kBlock / 32];
+    __shared__ double2 red[kFinalize / 32];
     const int s = blockIdx.x;
     double sum = 0.0, comp = 0.0;
+#pragma unroll 4
     for (uint32_t b = threadIdx.x; b < blocks; b += blockDim.x) {
         const double2 v = partials[(size_t)b * n + s];
         two_sum_merge(sum, comp, v.x, v.y);
@@ -268,10 +276,10 @@ cudaError_t launch_step(const lbms_t* h, int src, bool mass, cudaStream_t st)
 cudaError_t launch_finalize(const lbms_t* h, cudaStream_t st)
 {
     if (h->dtype == LBMS_F32)
-        k_mass_finalize_fixed<<<h->n, kBlock, 0, st>>>(static_cast<const long long*>(h->partials),
+        k_mass_finalize_fixed<<<h->n, kFinalize, 0, st>>>(static_cast<const long long*>(h->partials),
                                                          h->blocks, h->n, h->fixed_shift, h->mass_dev);
     else
-        k_mass_finalize_pairs<<<h->n, kBlock, 0, st>>>(static_cast<const double2*>(h->partials),
+        k_mass_finalize_pairs<<<h->n, kFinalize, 0, st>>>(static_cast<const double2*>(h->partials),
                                                          h->blocks, h->n, h->mass_dev);
     return cudaGetLastError();
 }
@@ -319,10 +327,10 @@ cudaError_t launch_mass_reduce(int dtype, const void* partials, uint32_t blocks,
                                double* out, cudaStream_t stream)
 {
     if (dtype == LBMS_F32)
-        k_mass_finalize_fixed<<<n, kBlock, 0, stream>>>(static_cast<const long long*>(partials), blocks,
+        k_mass_finalize_fixed<<<n, kFinalize, 0, stream>>>(static_cast<const long long*>(partials), blocks,
                                                           n, shift, out);
     else
-        k_mass_finalize_pairs<<<n, kBlock, 0, stream>>>(static_cast<const double2*>(partials), blocks, n,
+        k_mass_finalize_pairs<<<n, kFinalize, 0, stream>>>(static_cast<const double2*>(partials), blocks, n,
                                                           out);
     return cudaGetLastError();
 }
@@ -794,6 +802,8 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
 }
 
 long lbms_steps_done(const lbms_t* h) { return h ? h->steps : -1; }
+
+const void* lbms_populations(const lbms_t* h) { return h ? h->f[h->cur] : nullptr; }
 
 const char* lbms_last_error(const lbms_t* h) { return h ? h->err : g_create_error; }
 

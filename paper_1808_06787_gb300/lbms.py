@@ -38,7 +38,8 @@ ERRORS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ERANGE", 6:
 EXPORTED = (
     "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_set_boundary", "lbms_step",
     "lbms_moments", "lbms_gradient",
-    "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_last_error",
+    "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_populations",
+    "lbms_last_error",
     "lbms_destroy",
     "lbms_batch_workspace_size", "lbms_batch_create", "lbms_batch_set_state", "lbms_batch_step",
     "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_schedule",
@@ -101,6 +102,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_status.restype = I
         L.lbms_steps_done.argtypes = [P]
         L.lbms_steps_done.restype = ctypes.c_long
+        L.lbms_populations.argtypes = [P]
+        L.lbms_populations.restype = P
         L.lbms_last_error.argtypes = [P]
         L.lbms_last_error.restype = ctypes.c_char_p
         L.lbms_destroy.argtypes = [P]
@@ -422,8 +425,7 @@ class Solver:
         nx, ny, nz = self.grid
         cells = nx * ny * nz
         nbytes = (self.n - 1) * q * cells * es
-        stride = (nbytes + 255) // 256 * 256
-        off = (self.steps_done % 2) * stride
+        off = int(load().lbms_populations(self._h)) - self.workspace.data_ptr()
         return self.workspace[off:off + nbytes].view(self.dtype).view(self.n - 1, q, cells)
 
     def status(self) -> int:

@@ -122,4 +122,5 @@ def test_null_handle_calls(lib):
     assert lib.lbms_mass(None, None) == 1
     assert lib.lbms_status(None, None) == 1
     assert lib.lbms_steps_done(None) == -1
+    assert lib.lbms_populations(None) is None
     lib.lbms_destroy(None)

@@ -354,3 +354,19 @@ def test_gradient_parity(case, dtype):
     assert np.abs(G.sum(axis=0)).max() <= 10 * TOL_G[dtype]
     x, J = s.moments(flux=True)
     assert np.abs(J.double().cpu().numpy() - Jo).max() <= TOL_J[dtype]
+
+
+def test_population_view_follows_raw_state_loads():
+    """Solver.populations() views the current buffer, also after a raw load at an
+    odd step count (lbms_populations)."""
+    from paper_1808_06787_gb300 import Solver
+
+    dims = (12, 10, 1)
+    s = Solver("D2Q5", sy.random_D(3, seed=3), dims, dtype=torch.float64)
+    s.set_state(torch.from_numpy(sy.sin_modes(3, *dims, amp=0.1, seed=4)).cuda())
+    s.step(3)
+    f = s.get_state()
+    s.set_state_raw(f, 7)
+    assert torch.equal(s.populations().reshape(f.shape), f)
+    s.step(1)
+    assert torch.equal(s.populations().reshape(f.shape), s.get_state())
