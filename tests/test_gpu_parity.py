@@ -370,3 +370,49 @@ def test_population_view_follows_raw_state_loads():
     assert torch.equal(s.populations().reshape(f.shape), f)
     s.step(1)
     assert torch.equal(s.populations().reshape(f.shape), s.get_state())
+
+
+def test_d3q15_tube_full_size_window():
+    """D3Q15 256^3 closed ternary tube (bench workload `tube15`), FP32: after T steps
+    the nodes near the interface depend only on nodes within T cells along x, so
+    the oracle on an x-window of the full y-z cross-section gives them exactly."""
+    from paper_1808_06787_gb300 import Solver
+    import oracle
+
+    D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
+    N, T, half = 256, 24, 40
+    s = Solver("D3Q15", D, (N, N, N), bc="noflux", dtype=torch.float32)
+    x0 = sy.two_bulb(N, N, N, width=4.0)
+    s.set_state(torch.from_numpy(x0).float().cuda())
+    m0 = s.mass()
+    s.step(T)
+    x = s.moments()[:, :, :, N // 2 - 8:N // 2 + 8].double().cpu().numpy()
+    # the window's own faces (no-flux) are more than T cells from the compared nodes
+    win = x0[:, :, :, N // 2 - half:N // 2 + half]
+    ref = oracle.run("D3Q15", D, win, T, bc=("noflux",) * 6)[:, :, :, half - 8:half + 8]
+    assert np.abs(x - ref).max() <= 2e-5
+    assert np.all(np.abs(s.mass() - m0) <= 1e-6 * np.abs(m0))
+    assert s.status() == 0
+
+
+def test_d1q3_line_full_size_window():
+    """D1Q3 line of 2^26 nodes (bench workload `line`), FP32: the interface region
+    after T steps against the oracle on a window of 2T + 128 nodes, and mass."""
+    from paper_1808_06787_gb300 import Solver
+    import oracle
+
+    D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
+    N, T = 1 << 26, 500
+    s = Solver("D1Q3", D, (N, 1, 1), bc=("noflux", "noflux") + ("periodic",) * 4,
+               dtype=torch.float32)
+    x0 = sy.two_bulb(N, 1, 1, width=4.0)
+    s.set_state(torch.from_numpy(x0).float().cuda())
+    m0 = s.mass()
+    s.step(T)
+    half = T + 64
+    x = s.moments()[:, :, :, N // 2 - 32:N // 2 + 32].double().cpu().numpy()
+    win = x0[:, :, :, N // 2 - half:N // 2 + half]
+    ref = oracle.run("D1Q3", D, win, T, bc=("noflux", "noflux") + ("periodic",) * 4)
+    assert np.abs(x - ref[:, :, :, half - 32:half + 32]).max() <= 2e-5
+    assert np.all(np.abs(s.mass() - m0) <= 1e-6 * np.abs(m0))
+    assert s.status() == 0
