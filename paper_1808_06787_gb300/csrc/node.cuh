@@ -4,7 +4,8 @@
 // relation D~ = c_s^2 (Lambda_1^{-1} - I/2) (Eq. 3-26),
 //     Lambda_1 = (B^{-1}/c_s^2 + I/2)^{-1} = K^{-1} B,   K = I/c_s^2 + B/2,
 // so one Gauss-Jordan elimination of [K | B] gives Lambda_1 without forming
-// B^{-1} (B need not even be invertible).  The elimination runs without
+// B^{-1} (B need not even be invertible); for ternary mixtures the 2 x 2 form
+// adj(K) B / det(K) does it with a single reciprocal.  The elimination runs without
 // pivoting: B has real non-negative eigenvalues (it is the reduced form of the
 // Maxwell-Stefan friction matrix, which is diagonally similar to a symmetric
 // positive semi-definite one), and every pivot of K has been found to be at
@@ -73,22 +74,33 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
             K[i][j] = T(0.5) * b + (i == j ? cs2inv : T(0));
         }
     }
+    if constexpr (S == 2) {
+        // ternary mixtures (Remark IV): Lambda_1 = adj(K) B / det(K), one reciprocal;
+        // det(K) > 0 because B's eigenvalues are real and non-negative
+        const T rdet = recip(K[0][0] * K[1][1] - K[0][1] * K[1][0]);
+        const T b00 = L1[0][0], b01 = L1[0][1], b10 = L1[1][0], b11 = L1[1][1];
+        L1[0][0] = (K[1][1] * b00 - K[0][1] * b10) * rdet;
+        L1[0][1] = (K[1][1] * b01 - K[0][1] * b11) * rdet;
+        L1[1][0] = (K[0][0] * b10 - K[1][0] * b00) * rdet;
+        L1[1][1] = (K[0][0] * b11 - K[1][0] * b01) * rdet;
+    } else {
 #pragma unroll
-    for (int p = 0; p < S; ++p) {
-        const T inv = recip(K[p][p]);
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            K[p][j] *= inv;
-            L1[p][j] *= inv;
-        }
-#pragma unroll
-        for (int r = 0; r < S; ++r) {
-            if (r == p) continue;
-            const T fac = K[r][p];
+        for (int p = 0; p < S; ++p) {
+            const T inv = recip(K[p][p]);
 #pragma unroll
             for (int j = 0; j < S; ++j) {
-                K[r][j] -= fac * K[p][j];
-                L1[r][j] -= fac * L1[p][j];
+                K[p][j] *= inv;
+                L1[p][j] *= inv;
+            }
+#pragma unroll
+            for (int r = 0; r < S; ++r) {
+                if (r == p) continue;
+                const T fac = K[r][p];
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    K[r][j] -= fac * K[p][j];
+                    L1[r][j] -= fac * L1[p][j];
+                }
             }
         }
     }
@@ -97,10 +109,18 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
 #pragma unroll
         for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
     if (relax == LBMS_RELAX_MAGIC) {
+        if constexpr (S == 2) {
+            // Eq. 3-16 for both diagonal entries with one reciprocal
+            const T a = L1[0][0] - T(8), b = L1[1][1] - T(8);
+            const T r = recip(a * b);
+            L2[0][0] = T(8) * (L1[0][0] - T(2)) * (b * r);
+            L2[1][1] = T(8) * (L1[1][1] - T(2)) * (a * r);
+        } else {
 #pragma unroll
-        for (int i = 0; i < S; ++i) {
-            const T l = L1[i][i];
-            L2[i][i] = T(8) * (l - T(2)) * recip(l - T(8));  // Eq. 3-16, i == j
+            for (int i = 0; i < S; ++i) {
+                const T l = L1[i][i];
+                L2[i][i] = T(8) * (l - T(2)) * recip(l - T(8));  // Eq. 3-16, i == j
+            }
         }
     }
 }
