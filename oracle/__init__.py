@@ -30,7 +30,7 @@ _lock = threading.Lock()
 _lib = None
 
 LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4}
-RELAX = {"magic": 0, "srt": 1}
+RELAX = {"magic": 0, "srt": 1, "frozen": 2}
 BC = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 
 
@@ -69,6 +69,7 @@ def lib():
             L.orc_run.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P, P]
             L.orc_run_snap.argtypes = [I, I, I, I, I, P, I, P, P, P, ctypes.c_long, P, P, P,
                                        I, P, P]
+            L.orc_set_reference.argtypes = [I, P]
             L.orc_set_threads.argtypes = [I]
             L.orc_get_threads.restype = I
             _lib = L
@@ -159,14 +160,16 @@ def collide_node(lattice: str, D, fs, relax: str = "magic") -> np.ndarray:
 
 
 def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "magic",
-        flux: bool = False, snapshots=None, xb=None, grad: bool = False):
+        flux: bool = False, snapshots=None, xb=None, grad: bool = False, xi_ref=None):
     """Run the scheme from f = f_eq(x0) for ``steps`` steps.
 
     ``x0`` is [n, nz, ny, nx] (all n species).  ``bc`` names the six faces
     (x-low, x-high, y-low, y-high, z-low, z-high) "periodic", "noflux" or
     "dirichlet"; ``xb`` is [6, n], the composition held on each Dirichlet face
     (rows of other faces are ignored).  Returns ``x`` of the same shape at
-    t = steps; with ``flux=True`` also ``J`` of shape [n, dim, nz, ny, nx]; with
+    t = steps; ``relax="frozen"`` evaluates the relaxation matrices (and the
+    flux's D~) at the fixed composition ``xi_ref`` (n values), which makes the
+    scheme linear.  With ``flux=True`` also ``J`` of shape [n, dim, nz, ny, nx]; with
     ``grad=True`` also the local gradients of Eq. xix, same shape; with
     ``snapshots`` (ascending step counts <= steps) also the mole-fraction fields
     at those steps, shape [len(snapshots), n, nz, ny, nx].
@@ -176,6 +179,10 @@ def run(lattice: str, D, x0, steps: int, *, bc=("periodic",) * 6, relax: str = "
     n, nz, ny, nx = x0.shape
     q, dim = lattice_info(lattice)[:2]
     bcs = np.asarray([BC[b] if isinstance(b, str) else int(b) for b in bc], dtype=np.int32)
+    if relax == "frozen":
+        ref = _f64(np.asarray(xi_ref, dtype=np.float64).reshape(-1))
+        if ref.size != n or lib().orc_set_reference(n, _p(ref)) != 0:
+            raise ValueError("relax='frozen' needs xi_ref with n mole fractions")
     if xb is not None:
         xb = _f64(np.nan_to_num(np.asarray(xb, dtype=np.float64)).reshape(6, n))
     xo = np.zeros_like(x0)

@@ -18,7 +18,9 @@
  *      1/4 for D3Q7; the paper derives Eq. 3-26 for D2Q5 only).
  *   5. Lambda_2 by Eq. 3-16 (off-diagonal = Lambda_1, diagonal
  *      8 (l - 2) / (l - 8)); or Lambda_2 = Lambda_1 in the single-relaxation-time
- *      reduction; lambda_0 = 1 (Sec. 3.1).
+ *      reduction; lambda_0 = 1 (Sec. 3.1).  A third, frozen mode evaluates steps
+ *      2-5 (and D~ of the flux) at a fixed reference composition instead of the
+ *      local one, which makes the scheme linear (a test mode; Eq. 3-16 rule).
  *   6. Collision in moment space, Eq. 3-13a: m = M f, m_eq = M (w_k xi),
  *      m+_a = m_a - sum_j lambda_{g(a)}^{ij} (m^j_a - m^j_eq,a), f+ = M^{-1} m+,
  *      with M built explicitly from the moment polynomials and M^{-1} obtained by
@@ -60,7 +62,7 @@
 #define ORC_MAXN 8
 
 enum { ORC_D2Q5 = 0, ORC_D2Q9 = 1, ORC_D3Q7 = 2, ORC_D3Q15 = 3, ORC_D1Q3 = 4 };
-enum { ORC_MAGIC = 0, ORC_SRT = 1 };
+enum { ORC_MAGIC = 0, ORC_SRT = 1, ORC_FROZEN = 2 };
 enum { ORC_PERIODIC = 0, ORC_NOFLUX = 1, ORC_DIRICHLET = 2 };
 enum { GRP_CONSERVED = 0, GRP_ODD = 1, GRP_EVEN = 2 };
 
@@ -298,13 +300,22 @@ static int ms_Dtilde(int n, const double* xi, const double* D, double* Dt)
     return gj_inverse(n - 1, B, Dt);
 }
 
+/* Reference composition of the frozen mode (all n species). */
+static double g_xref[ORC_MAXN];
+
+/* The composition the relaxation matrices are evaluated at. */
+static const double* lambda_xi(int relax, const double* xi)
+{
+    return relax == ORC_FROZEN ? g_xref : xi;
+}
+
 /* Lambda_1 from Eq. 3-26 and Lambda_2 from Eq. 3-16 (or = Lambda_1 for SRT). */
 static int ms_lambdas(int n, const double* xi, const double* D, double cs2, int relax,
                       double* L1, double* L2)
 {
     int S = n - 1;
     double Dt[ORC_MAXN * ORC_MAXN], A[ORC_MAXN * ORC_MAXN];
-    if (ms_Dtilde(n, xi, D, Dt)) return -1;
+    if (ms_Dtilde(n, lambda_xi(relax, xi), D, Dt)) return -1;
     for (int i = 0; i < S; ++i)
         for (int j = 0; j < S; ++j) A[i * S + j] = Dt[i * S + j] / cs2 + (i == j ? 0.5 : 0.0);
     if (gj_inverse(S, A, L1)) return -1;
@@ -419,6 +430,14 @@ int orc_Dtilde(int n, const double* xi, const double* D, double* Dt)
 {
     if (n < 2 || n > ORC_MAXN) return -1;
     return ms_Dtilde(n, xi, D, Dt);
+}
+
+/* Sets the reference composition (n mole fractions) of the frozen mode. */
+int orc_set_reference(int n, const double* xi_ref)
+{
+    if (n < 2 || n > ORC_MAXN || !xi_ref) return -1;
+    for (int s = 0; s < n; ++s) g_xref[s] = xi_ref[s];
+    return 0;
 }
 
 int orc_lambdas(int lat, int n, const double* xi, const double* D, int relax,
@@ -548,7 +567,8 @@ int orc_run_snap(int lat, int n, int nx, int ny, int nz, const double* D, int re
             double Gn[3] = {0.0, 0.0, 0.0};
             double L1[ORC_MAXN * ORC_MAXN], L2[ORC_MAXN * ORC_MAXN], Dt[ORC_MAXN * ORC_MAXN];
             node_xi(&L, n, &f[c * per], xi);
-            if (ms_lambdas(n, xi, D, L.cs2, relax, L1, L2) || ms_Dtilde(n, xi, D, Dt)) {
+            if (ms_lambdas(n, xi, D, L.cs2, relax, L1, L2) ||
+                ms_Dtilde(n, lambda_xi(relax, xi), D, Dt)) {
                 err = 1;
                 break;
             }

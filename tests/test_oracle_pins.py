@@ -328,6 +328,42 @@ def test_ternary_linear_response_exact(lat):
     np.testing.assert_allclose(jresp.sum(axis=0), 0.0, atol=1e-10)
 
 
+@pytest.mark.parametrize("lat", LATTICES)
+def test_frozen_mode_is_linear_and_exact(lat):
+    """Relaxation matrices frozen at xi_ref make the ternary scheme linear: a
+    finite-amplitude mode equals the exact amplification G(theta)^t with
+    Lambda_1 from the closed-form D~(xi_ref) of Remark IV, fluxes included."""
+    o = _oracle()
+    c, w = th.golden_lattice(lat)
+    cs2 = th.cs2_of(c, w)
+    dims = {"D2Q5": (16, 6, 1), "D2Q9": (12, 8, 1), "D3Q7": (8, 4, 6), "D3Q15": (6, 4, 5),
+            "D1Q3": (16, 1, 1)}[lat]
+    k = {"D2Q5": (1, 1, 0), "D2Q9": (1, 1, 0), "D3Q7": (1, 0, 1), "D3Q15": (1, 1, 1),
+         "D1Q3": (1, 0, 0)}[lat]
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    D12, D13, D23 = 0.10, 0.08, 0.02
+    D = sy.D_from_pairs(3, {(1, 2): D12, (1, 3): D13, (2, 3): D23})
+    xref = np.array([0.3, 0.25, 0.45])
+    v = np.array([1.0, -0.4, -0.6])
+    eps = 0.1  # far from the small-amplitude limit: exactness comes from linearity
+    steps = 60
+    x, J = o.run(lat, D, sy.small_mode(xref, v, eps, nx, ny, nz, k=k), steps, flux=True,
+                 relax="frozen", xi_ref=xref)
+    L1 = th.lambda1_from_Dtilde(th.ternary_Dtilde_closed(xref, D12, D13, D23), cs2)
+    L2 = th.magic_lambda2(L1)
+    theta = th.theta_of(k, shape)
+    xi_hat, m1_hat = th.predict_mode(c, w, L1, L2, theta, eps * v, steps)
+    for s in range(2):
+        np.testing.assert_allclose(x[s], xref[s] + th.mode_field(xi_hat[s], theta, shape),
+                                   rtol=0, atol=1e-14)
+    J_hat = (np.eye(2) - 0.5 * L1) @ m1_hat
+    for s in range(2):
+        for a in range(J.shape[1]):
+            np.testing.assert_allclose(J[s, a], th.mode_field(J_hat[s, a], theta, shape),
+                                       rtol=0, atol=1e-14)
+
+
 # --------------------------------------------------------------------------
 # Continuum limit (Chapman-Enskog, Eq. 3-26; second-order convergence)
 # --------------------------------------------------------------------------
