@@ -65,8 +65,12 @@ enum { LBMS_PERIODIC = 0, LBMS_NOFLUX = 1, LBMS_DIRICHLET = 2 };
 /* Relaxation of the even moments.  MAGIC: Lambda_2 by Eq. 3-16 (off-diagonal
  * entries equal Lambda_1, diagonal 8 (l - 2) / (l - 8)).  SRT: Lambda_2 =
  * Lambda_1, the single-relaxation-time reduction of Sec. 3.1 used for the
- * comparison of Sec. 4.1. */
-enum { LBMS_RELAX_MAGIC = 0, LBMS_RELAX_SRT = 1 };
+ * comparison of Sec. 4.1.  FROZEN: as MAGIC, but Lambda_1 and Lambda_2 (and D~
+ * of the flux) are evaluated at a fixed reference composition set with
+ * lbms_set_reference instead of each node's own: the scheme becomes linear,
+ * which test suites use to compare against exact Fourier amplification; it is
+ * not a model of the paper. */
+enum { LBMS_RELAX_MAGIC = 0, LBMS_RELAX_SRT = 1, LBMS_RELAX_FROZEN = 2 };
 
 /* Return codes. */
 enum {
@@ -108,7 +112,9 @@ size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dt
  *   D          host array of n * n binary Maxwell-Stefan diffusivities D_ij in
  *              lattice units (Eq. 2-7), row-major.  Off-diagonal entries must be
  *              finite, > 0 and symmetric (D_ij = D_ji); the diagonal is ignored.
- *   relax      LBMS_RELAX_MAGIC | LBMS_RELAX_SRT.
+ *   relax      LBMS_RELAX_MAGIC | LBMS_RELAX_SRT | LBMS_RELAX_FROZEN (the last
+ *              needs lbms_set_reference before the first step; the adjoint
+ *              entry points reject it).
  *   bc         host array of 6 face kinds {x-low, x-high, y-low, y-high, z-low,
  *              z-high}, each LBMS_PERIODIC, LBMS_NOFLUX or LBMS_DIRICHLET; a
  *              periodic face must be paired with a periodic face on the same
@@ -149,6 +155,14 @@ int lbms_set_state(lbms_t* h, const void* x0);
  * fails.
  */
 int lbms_set_boundary(lbms_t* h, int face, const double* xi_b);
+
+/*
+ * Reference composition of a LBMS_RELAX_FROZEN handle: xi_ref is a host array
+ * of all n mole fractions, each in [0, 1], summing to 1 within 1e-6.  Applies
+ * to the steps and moments issued after the call.  Returns LBMS_EINVAL for
+ * another relaxation mode or a bad composition.
+ */
+int lbms_set_reference(lbms_t* h, const double* xi_ref);
 
 /*
  * Advance n_steps >= 0 time steps of Eqs. 3-13a/3-13b (pull form: each node

@@ -13,7 +13,18 @@ namespace lbms {
 template <typename T>
 struct Coeffs {
     T invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES];
+    T xref[LBMS_MAX_SPECIES];  // reference composition of LBMS_RELAX_FROZEN
 };
+
+// The composition the relaxation matrices are evaluated at: the node's own, or
+// the fixed reference of the frozen mode (a test mode that makes the scheme linear).
+template <int S, typename T>
+__device__ __forceinline__ void lambda_composition(const T (&xi)[S + 1], const Coeffs<T>& co,
+                                                   int relax, T (&xl)[S + 1])
+{
+#pragma unroll
+    for (int s = 0; s <= S; ++s) xl[s] = relax == LBMS_RELAX_FROZEN ? co.xref[s] : xi[s];
+}
 
 // Mass partials.  FP32 solvers accumulate each node's mole fraction as a signed
 // 64-bit fixed-point number xi * 2^shift (exact integer sums, independent of
@@ -162,7 +173,9 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
         mole_fractions<LAT, S, T>(f, xi);
         if (MASS) check_range<S, T>(xi, p.status);  // once per lbms_step call
         T L1[S][S], L2[S][S];
-        relaxation_matrices<S, T>(xi, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
+        T xl[S + 1];
+        lambda_composition<S, T>(xi, p.co, p.relax, xl);
+        relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
         collide<LAT, S, T>(f, xi, L1, L2, mix32(step * 0x9e3779b9u) ^ (cell * 0x27d4eb2du));
 #pragma unroll
         for (int s = 0; s < S; ++s)
@@ -279,7 +292,9 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         T L1[S][S], L2[S][S];
-        relaxation_matrices<S, T>(xi, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
+        T xl[S + 1];
+        lambda_composition<S, T>(xi, p.co, p.relax, xl);
+        relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
         flux_and_gradient<LAT, S, T>(f, L1, J, G);
     }
     if (p.J_out)
@@ -298,8 +313,10 @@ template <typename T>
 Coeffs<T> make_coeffs(const KArgs& a)
 {
     Coeffs<T> c;
-    for (int i = 0; i < LBMS_MAX_SPECIES; ++i)
+    for (int i = 0; i < LBMS_MAX_SPECIES; ++i) {
         for (int j = 0; j < LBMS_MAX_SPECIES; ++j) c.invD[i][j] = (T)a.invD[i][j];
+        c.xref[i] = (T)a.xref[i];
+    }
     return c;
 }
 

@@ -184,6 +184,8 @@ struct lbms_s {
     void* xb = nullptr;      // device [6][S] compositions of the Dirichlet faces, solver dtype
     size_t es = 4;
     double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};
+    double xref[LBMS_MAX_SPECIES] = {};  // reference composition (frozen mode)
+    bool xref_set = false;
     char* ws = nullptr;
     Layout lay{};
     void* f[2] = {nullptr, nullptr};
@@ -255,6 +257,7 @@ KArgs base_args(const lbms_t* h, cudaStream_t st)
     a.relax = h->relax;
     a.n_species = h->n;
     memcpy(a.invD, h->invD, sizeof(a.invD));
+    memcpy(a.xref, h->xref, sizeof(a.xref));
     a.status = h->status;
     a.fixed_shift = h->fixed_shift;
     a.stream = st;
@@ -364,7 +367,7 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     Layout L;
     if (!make_layout(lattice, n_species, grid, dtype, &L))
         return fail(nullptr, LBMS_EINVAL, "invalid lattice/species/grid/dtype combination");
-    if (relax != LBMS_RELAX_MAGIC && relax != LBMS_RELAX_SRT)
+    if (relax != LBMS_RELAX_MAGIC && relax != LBMS_RELAX_SRT && relax != LBMS_RELAX_FROZEN)
         return fail(nullptr, LBMS_EINVAL, "invalid relaxation mode %d", relax);
     if (!D || !bc) return fail(nullptr, LBMS_EINVAL, "D and bc must not be NULL");
     if (!workspace) return fail(nullptr, LBMS_EINVAL, "workspace is NULL");
@@ -511,6 +514,31 @@ int lbms_set_boundary(lbms_t* h, int face, const double* xi_b)
     return LBMS_OK;
 }
 
+int lbms_set_reference(lbms_t* h, const double* xi_ref)
+{
+    if (!h) return LBMS_EINVAL;
+    if (h->relax != LBMS_RELAX_FROZEN)
+        return fail(h, LBMS_EINVAL, "the handle's relaxation mode is not LBMS_RELAX_FROZEN");
+    if (!xi_ref) return fail(h, LBMS_EINVAL, "xi_ref is NULL");
+    double sum = 0.0;
+    for (int s = 0; s < h->n; ++s) {
+        if (!isfinite(xi_ref[s]) || xi_ref[s] < 0.0 || xi_ref[s] > 1.0)
+            return fail(h, LBMS_EINVAL, "xi_ref[%d] = %g is not a mole fraction", s, xi_ref[s]);
+        sum += xi_ref[s];
+    }
+    if (fabs(sum - 1.0) > 1e-6) return fail(h, LBMS_EINVAL, "xi_ref sums to %.9g, not 1", sum);
+    h->err[0] = '\0';
+    for (int s = 0; s < h->n; ++s) h->xref[s] = xi_ref[s];
+    h->xref_set = true;
+    // the captured step graphs carry the kernel arguments: capture them again
+    for (int i = 0; i < 2; ++i)
+        if (h->graph[i]) {
+            cudaGraphExecDestroy(h->graph[i]);
+            h->graph[i] = nullptr;
+        }
+    return LBMS_OK;
+}
+
 int lbms_step(lbms_t* h, long n_steps)
 {
     if (!h) return LBMS_EINVAL;
@@ -518,6 +546,8 @@ int lbms_step(lbms_t* h, long n_steps)
     if (h->dirichlet & ~h->xb_set)
         return fail(h, LBMS_EINVAL, "Dirichlet face mask 0x%x has no composition set",
                     h->dirichlet & ~h->xb_set);
+    if (h->relax == LBMS_RELAX_FROZEN && !h->xref_set)
+        return fail(h, LBMS_EINVAL, "LBMS_RELAX_FROZEN needs lbms_set_reference first");
     h->err[0] = '\0';
     if (n_steps == 0) return LBMS_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -705,6 +735,8 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
     if (h->dirichlet & ~h->xb_set)
         return fail(h, LBMS_EINVAL, "Dirichlet face mask 0x%x has no composition set",
                     h->dirichlet & ~h->xb_set);
+    if (h->relax == LBMS_RELAX_FROZEN && !h->xref_set)
+        return fail(h, LBMS_EINVAL, "LBMS_RELAX_FROZEN needs lbms_set_reference first");
     h->err[0] = '\0';
     if (count == 0) return LBMS_OK;
     const size_t elems = (size_t)h->S * h->Q * h->cells;
@@ -732,7 +764,7 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
 
 size_t lbms_adjoint_scratch_size(const lbms_t* h)
 {
-    if (!h || h->S > 4) return 0;
+    if (!h || h->S > 4 || h->relax == LBMS_RELAX_FROZEN) return 0;
     return (size_t)node_blocks(h->cells) * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
 }
 
@@ -740,6 +772,7 @@ int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
 {
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!grad_x || !lam) return fail(h, LBMS_EINVAL, "grad_x and lam must not be NULL");
     AArgs a;
     a.k = base_args(h, h->stream);
@@ -753,6 +786,7 @@ int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* l
 {
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!f_prev || !lam_in || !lam_out || !gacc)
         return fail(h, LBMS_EINVAL, "f_prev, lam_in, lam_out and gacc must not be NULL");
     if (lam_in == lam_out) return fail(h, LBMS_EINVAL, "lam_in and lam_out must be different buffers");
@@ -770,6 +804,7 @@ int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
 {
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!lam0 || !grad_x0) return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must not be NULL");
     AArgs a;
     a.k = base_args(h, h->stream);
@@ -783,6 +818,7 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
 {
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!gacc || !dL_dD) return fail(h, LBMS_EINVAL, "gacc and dL_dD must not be NULL");
     const int np = h->n * (h->n - 1) / 2;
     double* slot = reinterpret_cast<double*>(reinterpret_cast<char*>(h->status) + 128);

@@ -39,6 +39,7 @@ struct KArgs {
     int relax = LBMS_RELAX_MAGIC;
     int n_species = 2;
     double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};  // 1 / D_ij
+    double xref[LBMS_MAX_SPECIES] = {};                    // reference composition (frozen mode)
     void* partials = nullptr;  // [blocks][n]: int64 fixed point (FP32) or double2 (FP64)
     int fixed_shift = 32;      // fraction bits of the FP32 fixed-point mass partials
     uint32_t* status = nullptr;

@@ -50,7 +50,8 @@ namespace lbms {
 __device__ __forceinline__ float recip(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 
-// Lambda_1 = K^{-1} B and Lambda_2 (Eq. 3-16 or SRT) from all S+1 mole fractions.
+// Lambda_1 = K^{-1} B and Lambda_2 (Eq. 3-16, or = Lambda_1 for SRT) from all S+1
+// mole fractions.
 template <int S, typename T, typename InvD>
 __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const InvD& invD,
                                                     T cs2inv, int relax, T (&L1)[S][S],
@@ -108,7 +109,7 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
     for (int i = 0; i < S; ++i)
 #pragma unroll
         for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
-    if (relax == LBMS_RELAX_MAGIC) {
+    if (relax != LBMS_RELAX_SRT) {  // Eq. 3-16 (the frozen mode uses it too)
         if constexpr (S == 2) {
             // Eq. 3-16 for both diagonal entries with one reciprocal
             const T a = L1[0][0] - T(8), b = L1[1][1] - T(8);

@@ -25,7 +25,7 @@ from . import build as _build
 LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4}
 DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q15": 3, "D1Q3": 1}
 Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7, "D3Q15": 15, "D1Q3": 3}
-RELAX = {"magic": 0, "srt": 1}
+RELAX = {"magic": 0, "srt": 1, "frozen": 2}
 FACE = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 DTYPES = {torch.float32: 0, torch.float64: 1}
 
@@ -36,7 +36,8 @@ FLAG_INIT = 0x4
 ERRORS = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ERANGE", 6: "ETIMEOUT"}
 
 EXPORTED = (
-    "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_set_boundary", "lbms_step",
+    "lbms_workspace_size", "lbms_create", "lbms_set_state", "lbms_set_boundary",
+    "lbms_set_reference", "lbms_step",
     "lbms_moments", "lbms_gradient",
     "lbms_mass", "lbms_mass_noalloc", "lbms_status", "lbms_steps_done", "lbms_populations",
     "lbms_last_error",
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_set_state.restype = I
         L.lbms_set_boundary.argtypes = [P, I, P]
         L.lbms_set_boundary.restype = I
+        L.lbms_set_reference.argtypes = [P, P]
+        L.lbms_set_reference.restype = I
         L.lbms_step.argtypes = [P, ctypes.c_long]
         L.lbms_step.restype = I
         L.lbms_moments.argtypes = [P, P, P]
@@ -204,6 +207,11 @@ def lbms_set_boundary(h, face: int, xi_b) -> None:
            "lbms_set_boundary")
 
 
+def lbms_set_reference(h, xi_ref) -> None:
+    v = np.ascontiguousarray(np.asarray(xi_ref, dtype=np.float64).reshape(-1))
+    _check(h, load().lbms_set_reference(h, v.ctypes.data_as(ctypes.c_void_p)), "lbms_set_reference")
+
+
 def lbms_step(h, n_steps: int) -> None:
     _check(h, load().lbms_step(h, int(n_steps)), "lbms_step")
 
@@ -261,14 +269,16 @@ class Solver:
     lattice units; ``grid``: (nx, ny[, nz]); ``bc``: one kind for all faces or six
     kinds (x-, x+, y-, y+, z-, z+), each "periodic", "noflux" or "dirichlet";
     ``boundary``: {face index: composition of all n species} for the Dirichlet
-    faces (see ``set_boundary``); ``relax``: "magic" (Eq. 3-16) or "srt";
+    faces (see ``set_boundary``); ``relax``: "magic" (Eq. 3-16), "srt", or
+    "frozen" (relaxation matrices at the fixed composition ``reference``, a
+    linear test mode);
     ``dtype``: torch.float32 or torch.float64.  Work is ordered on ``stream``
     (default: the current torch stream of ``device``).
     """
 
     def __init__(self, lattice: str, D, grid: Sequence[int], *, bc="periodic",
                  relax: str = "magic", dtype=torch.float32, device="cuda",
-                 stream: Optional[torch.cuda.Stream] = None, boundary=None):
+                 stream: Optional[torch.cuda.Stream] = None, boundary=None, reference=None):
         if not torch.cuda.is_available():
             raise LbmsError("the lbms solver needs a CUDA device")
         self.lattice = lattice
@@ -290,6 +300,12 @@ class Solver:
                               self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
         for face, xi_b in (boundary or {}).items():
             self.set_boundary(face, xi_b)
+        if reference is not None:
+            self.set_reference(reference)
+
+    def set_reference(self, xi_ref) -> None:
+        """Reference composition (all n species) of a "frozen" solver."""
+        lbms_set_reference(self._h, xi_ref)
 
     def set_boundary(self, face: int, xi_b) -> None:
         """Composition (all n species) held on Dirichlet face ``face`` (0..5 as in
@@ -391,7 +407,7 @@ class Solver:
     def adjoint_scratch(self) -> torch.Tensor:
         nbytes = int(load().lbms_adjoint_scratch_size(self._h))
         if nbytes == 0:
-            raise LbmsError("the adjoint supports up to 5 species")
+            raise LbmsError("the adjoint supports up to 5 species and not the frozen mode")
         return torch.zeros(nbytes // 8, dtype=torch.float64, device=self.device)
 
     def adjoint_seed(self, grad_x: torch.Tensor, lam: torch.Tensor) -> None:

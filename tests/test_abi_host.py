@@ -100,7 +100,7 @@ def test_create_validates_before_device_work(lib):
     assert rc == 1 and "face kind" in msg
     rc, _, msg = _create(lib, bc=(2, 0, 0, 0, 0, 0))  # Dirichlet against a periodic face
     assert rc == 1 and "paired" in msg
-    rc, _, msg = _create(lib, relax=5)
+    rc, _, msg = _create(lib, relax=3)
     assert rc == 1 and "relaxation" in msg
     rc, _, msg = _create(lib, ws=0)
     assert rc == 1 and "workspace" in msg
@@ -118,6 +118,7 @@ def test_null_handle_calls(lib):
     assert lib.lbms_step(None, 1) == 1
     assert lib.lbms_set_state(None, None) == 1
     assert lib.lbms_set_boundary(None, 0, None) == 1
+    assert lib.lbms_set_reference(None, None) == 1
     assert lib.lbms_moments(None, None, None) == 1
     assert lib.lbms_mass(None, None) == 1
     assert lib.lbms_status(None, None) == 1

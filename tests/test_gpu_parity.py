@@ -416,3 +416,45 @@ def test_d1q3_line_full_size_window():
     assert np.abs(x - ref[:, :, :, half - 32:half + 32]).max() <= 2e-5
     assert np.all(np.abs(s.mass() - m0) <= 1e-6 * np.abs(m0))
     assert s.status() == 0
+
+
+FROZEN_CASES = [
+    ("D2Q5", 3, (24, 18, 1), (P, P, W, W, P, P)),
+    ("D2Q9", 4, (17, 13, 1), (P, P, P, P, P, P)),
+    ("D3Q7", 3, (11, 9, 7), (W, W, P, P, W, W)),
+    ("D3Q15", 3, (8, 7, 6), (P, P, P, P, P, P)),
+    ("D1Q3", 5, (41, 1, 1), (W, W, P, P, P, P)),
+]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("case", FROZEN_CASES, ids=lambda c: "%s-n%d" % (c[0], c[1]))
+def test_frozen_mode_parity(case, dtype):
+    """LBMS_RELAX_FROZEN (relaxation matrices at a fixed reference composition)
+    against the oracle's frozen mode: fields, fluxes and gradients."""
+    import oracle
+
+    from paper_1808_06787_gb300 import LbmsError, Solver
+
+    lattice, n, dims, bc = case
+    x0, D = _small_input(lattice, n, dims, 700 + n)
+    xref = np.full(n, 1.0 / n)
+    s = Solver(lattice, D, dims, bc=bc, relax="frozen", dtype=dtype)
+    s.set_state(torch.from_numpy(x0).to(dtype).cuda())
+    with pytest.raises(LbmsError, match="set_reference"):
+        s.step(1)
+    s.set_reference(xref)
+    s.step(211)
+    x, J = s.moments(flux=True)
+    G = s.gradient()
+    xo, Jo, Go = oracle.run(lattice, D, x0, 211, bc=bc, relax="frozen", xi_ref=xref,
+                            flux=True, grad=True)
+    assert np.abs(x.double().cpu().numpy() - xo).max() <= TOL_X[dtype]
+    assert np.abs(J.double().cpu().numpy() - Jo).max() <= TOL_J[dtype]
+    assert np.abs(G.double().cpu().numpy() - Go).max() <= TOL_G[dtype]
+    assert s.status() == 0
+    with pytest.raises(LbmsError):
+        s.set_reference(np.full(n, 0.5))  # does not sum to one
+    assert s.adjoint_scratch is not None
+    with pytest.raises(LbmsError, match="adjoint"):
+        s.adjoint_scratch()
