@@ -165,3 +165,10 @@ def test_config4_full_size_4096_instances():
         x0 = sy.batch_field(i, int(grids[i][0]))
         xr, _, _ = _single("D2Q5", Ds[i], x0, 5000, bcs[i], torch.float32)
         assert torch.equal(xs[i], xr), i
+    # two sampled instances (a periodic sine and a no-flux tanh one) against the oracle
+    import oracle
+
+    for i in (0, 1):
+        x0 = sy.batch_field(i, int(grids[i][0]))
+        ref = oracle.run("D2Q5", Ds[i], x0, 5000, bc=bcs[i])
+        assert np.abs(xs[i].double().cpu().numpy().reshape(ref.shape) - ref).max() <= 2e-5, i
