@@ -10,8 +10,9 @@ kernels from the last step to the first with sqrt(T) checkpointing: the
 forward keeps the populations every K = ceil(sqrt(T)) steps, and the backward
 pass recomputes each segment of K states from its checkpoint (bit for bit:
 the step count keys the stochastic rounding) before stepping the adjoint
-through it, so the extra cost is one forward pass and the memory is about
-2 sqrt(T) population buffers.
+through it, so the extra cost is one forward pass (run on a second stream,
+overlapping the adjoint steps) and the memory is about 3 sqrt(T) population
+buffers.
 """
 
 from __future__ import annotations
@@ -34,6 +35,7 @@ class RunSpec:
     relax: str = "magic"
     dtype: torch.dtype = torch.float32
     stats: dict = field(default_factory=dict)
+    boundary: dict = None  # {face: composition} of the Dirichlet faces
 
 
 def pairs_to_matrix(d_pairs, n: int) -> np.ndarray:
@@ -59,7 +61,7 @@ class MaxwellStefanLB(torch.autograd.Function):
         n = n_from_pairs(d_pairs.numel())
         D = pairs_to_matrix(d_pairs.detach().cpu().double().numpy(), n)
         solver = Solver(spec.lattice, D, spec.grid, bc=spec.bc, relax=spec.relax, dtype=spec.dtype,
-                        device=x0.device)
+                        device=x0.device, boundary=spec.boundary)
         solver.set_state(x0.detach().to(spec.dtype).contiguous())
         T = int(spec.steps)
         K = max(1, int(math.ceil(math.sqrt(T))))
@@ -75,6 +77,7 @@ class MaxwellStefanLB(torch.autograd.Function):
         xT = solver.moments()
         spec.stats["launches"] = launches + 1
         ctx.solver = solver
+        ctx.D = D
         ctx.x0_dtype = x0.dtype
         ctx.ckpts = ckpts
         ctx.K = K
@@ -87,23 +90,51 @@ class MaxwellStefanLB(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_xT: torch.Tensor):
         s = ctx.solver
+        spec = ctx.spec
         lam = s.adjoint_state()
         lam2 = torch.empty_like(lam)
         s.adjoint_seed(grad_xT.to(s.dtype), lam)
         gacc = s.adjoint_scratch()
-        seg = torch.empty((max(ctx.K - 1, 1),) + tuple(s.state_shape), dtype=s.dtype, device=s.device)
-        # optional timing of the adjoint-step loops (CUDA events on the solver's stream)
-        events = ctx.spec.stats.get("adjoint_events")
+        # Segment recomputation runs on a second stream through a second handle
+        # (its own step counters), one segment ahead of the adjoint steps, which
+        # are latency-bound and leave most of the GPU to it; two segment buffers
+        # alternate.  The results are those of the serial order, bit for bit.
+        side = torch.cuda.Stream(device=s.device)
+        side.wait_stream(s.stream)  # the checkpoints come from the forward
+        helper = Solver(spec.lattice, ctx.D, spec.grid, bc=spec.bc, relax=spec.relax,
+                        dtype=spec.dtype, device=s.device, stream=side, boundary=spec.boundary)
+        shape = (max(ctx.K - 1, 1),) + tuple(s.state_shape)
+        segs = [torch.empty(shape, dtype=s.dtype, device=s.device) for _ in range(2)]
+        order = list(reversed(ctx.ckpts))
+        rec_done, adj_done = [None] * len(order), [None] * len(order)
         launches = 1  # seed
-        for t0, ck in reversed(ctx.ckpts):
+
+        def recompute(i):
+            nonlocal launches
+            t0, ck = order[i]
+            count = min(t0 + ctx.K, ctx.T) - t0 - 1
+            if i >= 2:
+                side.wait_event(adj_done[i - 2])  # the buffer's previous segment is done
+            # f+(t0 + 1) .. f+(t1 - 1) from the checkpoint f+(t0)
+            helper.recompute(ck, t0, count, segs[i % 2])
+            launches += count + 2 if count > 0 else 0
+            ev = torch.cuda.Event()
+            ev.record(side)
+            rec_done[i] = ev
+
+        # optional timing of the adjoint-step loops (CUDA events on the solver's stream)
+        events = spec.stats.get("adjoint_events")
+        recompute(0)
+        for i, (t0, ck) in enumerate(order):
             t1 = min(t0 + ctx.K, ctx.T)
-            # recompute f+(t0 + 1) .. f+(t1 - 1) from the checkpoint f+(t0)
-            s.recompute(ck, t0, t1 - t0 - 1, seg)
-            launches += (t1 - t0 - 1) + 2 if t1 - t0 > 1 else 0
-            # adjoint steps t1 .. t0 + 1 (step t reads f+(t - 1))
+            if i + 1 < len(order):
+                recompute(i + 1)
+            s.stream.wait_event(rec_done[i])
+            seg = segs[i % 2]
             if events is not None:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e0.record(s.stream)
+            # adjoint steps t1 .. t0 + 1 (step t reads f+(t - 1))
             for t in range(t1, t0, -1):
                 s.adjoint_step(ck if t - 1 == t0 else seg[t - 2 - t0], lam, lam2, gacc)
                 lam, lam2 = lam2, lam
@@ -112,9 +143,12 @@ class MaxwellStefanLB(torch.autograd.Function):
                 e1 = torch.cuda.Event(enable_timing=True)
                 e1.record(s.stream)
                 events.append((e0, e1, t1 - t0))
+            ev = torch.cuda.Event()
+            ev.record(s.stream)
+            adj_done[i] = ev
         grad_x0 = s.adjoint_initial(lam).to(ctx.x0_dtype)
         gD = torch.from_numpy(s.adjoint_reduce(gacc))
-        ctx.spec.stats["launches"] = ctx.spec.stats.get("launches", 0) + launches + 2
+        spec.stats["launches"] = spec.stats.get("launches", 0) + launches + 2
         return grad_x0, gD, None
 
 
