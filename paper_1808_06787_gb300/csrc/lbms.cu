@@ -20,6 +20,9 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kStagingMax = size_t(16) << 20;  // host I/O chunk area
 constexpr int kGraphSteps = 32;                   // steps per captured graph (even)
+// captured run lengths: full runs of kGraphSteps, then the even remainder in
+// binary pieces (all even, so a run leaves the buffer parity unchanged)
+constexpr int kGraphLens[5] = {kGraphSteps, 16, 8, 4, 2};
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -199,7 +202,8 @@ struct lbms_s {
     char* staging = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // captured runs of kGraphLens[j] plain steps starting from buffer parity p
+    cudaGraphExec_t graph[2][5] = {};
     bool graphs_ok = true;
     long steps = 0;
     char err[512] = "";
@@ -298,13 +302,13 @@ bool is_device_ptr(const void* p)
 }
 
 // Capture kGraphSteps plain steps starting from buffer `parity`.
-cudaError_t build_graph(lbms_t* h, int parity)
+cudaError_t build_graph(lbms_t* h, int parity, int j)
 {
     cudaError_t e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
     int src = parity;
-    for (int i = 0; i < kGraphSteps && le == cudaSuccess; ++i) {
+    for (int i = 0; i < kGraphLens[j] && le == cudaSuccess; ++i) {
         le = launch_step(h, src, false, h->capture);
         src = 1 - src;
     }
@@ -315,7 +319,7 @@ cudaError_t build_graph(lbms_t* h, int parity)
         return le;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&h->graph[parity][j], g, 0);
     cudaGraphDestroy(g);
     return e;
 }
@@ -532,10 +536,11 @@ int lbms_set_reference(lbms_t* h, const double* xi_ref)
     h->xref_set = true;
     // the captured step graphs carry the kernel arguments: capture them again
     for (int i = 0; i < 2; ++i)
-        if (h->graph[i]) {
-            cudaGraphExecDestroy(h->graph[i]);
-            h->graph[i] = nullptr;
-        }
+        for (int j = 0; j < 5; ++j)
+            if (h->graph[i][j]) {
+                cudaGraphExecDestroy(h->graph[i][j]);
+                h->graph[i][j] = nullptr;
+            }
     return LBMS_OK;
 }
 
@@ -554,11 +559,11 @@ int lbms_step(lbms_t* h, long n_steps)
     cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
     const bool use_graphs = h->graphs_ok && cs == cudaStreamCaptureStatusNone;
-    long left = n_steps;
-    while (left > 1) {
-        if (use_graphs && left - 1 >= kGraphSteps) {
-            if (!h->graph[h->cur]) {
-                e = build_graph(h, h->cur);
+    long left = n_steps;  // the last step also writes the mass partials
+    for (int j = 0; use_graphs && j < 5; ++j) {
+        while (left - 1 >= kGraphLens[j] && use_graphs) {
+            if (!h->graph[h->cur][j]) {
+                e = build_graph(h, h->cur, j);
                 if (e != cudaSuccess) {
                     // fall back to direct launches for this handle
                     cudaGetLastError();
@@ -566,17 +571,12 @@ int lbms_step(lbms_t* h, long n_steps)
                     break;
                 }
             }
-            e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+            e = cudaGraphLaunch(h->graph[h->cur][j], h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
-            left -= kGraphSteps;
-            h->steps += kGraphSteps;
-            continue;
+            left -= kGraphLens[j];
+            h->steps += kGraphLens[j];
         }
-        e = launch_step(h, h->cur, false, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
-        h->cur = 1 - h->cur;
-        --left;
-        ++h->steps;
+        if (!h->graphs_ok) break;
     }
     while (left > 1) {
         e = launch_step(h, h->cur, false, h->stream);
@@ -847,7 +847,8 @@ void lbms_destroy(lbms_t* h)
 {
     if (!h) return;
     for (int i = 0; i < 2; ++i)
-        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        for (int j = 0; j < 5; ++j)
+            if (h->graph[i][j]) cudaGraphExecDestroy(h->graph[i][j]);
     if (h->capture) cudaStreamDestroy(h->capture);
     delete h;
 }
