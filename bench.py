@@ -412,7 +412,7 @@ BATCH_SOLVE_STEPS = 5000
 
 
 def run_batch(args):
-    """Config 4: 4096 independent ternary D2Q5 FP32 solves, square sides uniform
+    """Batched workload: 4096 independent ternary D2Q5 FP32 solves, square sides uniform
     in [32, 256], per-instance D_ij uniform in [0.01, 0.12], sine (periodic) or
     two-bulb tanh (no-flux x) initial fields; schedule chosen by the tuner."""
     import numpy as np
@@ -538,7 +538,7 @@ def run_batch(args):
 
 
 def run_adjoint(args):
-    """Config 5: gradient of the L2 misfit of the final mole fractions (ternary
+    """Adjoint workload: gradient of the L2 misfit of the final mole fractions (ternary
     D2Q5, 512^2, FP32, 4000 steps, target from D* = (0.09, 0.07, 0.02)) with
     respect to the three D_ij and the initial field, by the adjoint kernels
     with sqrt(T) checkpointing; the cost is reported against the plain forward

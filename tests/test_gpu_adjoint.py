@@ -161,7 +161,7 @@ def test_fp32_gradient_close_to_fp64_gradient_64():
     assert rel_x <= 5e-2, rel_x
 
 
-def test_config5_full_size_gradient_vs_finite_differences():
+def test_adjoint_512sq_full_size_gradient_vs_finite_differences():
     """512 x 512, 4000 steps, FP32: adjoint dL/dD against central differences
     (h = 1e-4) of the GPU forward; target generated with D* = (0.09, 0.07, 0.02)."""
     from paper_1808_06787_gb300 import RunSpec, Solver, simulate

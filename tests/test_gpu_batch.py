@@ -142,7 +142,7 @@ def test_tuner_picks_a_valid_schedule():
     assert np.all(times > 0) and times[chosen] == times.min()
 
 
-def test_config4_full_size_4096_instances():
+def test_batch_4096_uneven_d2q5_instances_full_size():
     """4096 ternary D2Q5 instances, sides uniform in [32, 256], 5000 steps, FP32:
     per-instance mass drift, flags, and sampled instances against single solves."""
     from paper_1808_06787_gb300 import BatchSolver

@@ -134,7 +134,7 @@ def test_flux_is_zero_at_t0_and_time_levels():
         assert np.abs(g["J"] - J).max() <= 1e-15
 
 
-def test_config1_d2q5_fp64_128_full():
+def test_d2q5_fp64_128sq_full_size():
     """128 x 128 periodic ternary D2Q5, FP64, 2000 steps, seeded sine modes."""
     D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
     x0 = sy.sin_modes(3, 128, 128, amp=0.05, seed=1001)
@@ -146,7 +146,7 @@ def test_config1_d2q5_fp64_128_full():
     assert np.all(np.abs(g["mass"] - m0) <= 1e-12 * m0)
 
 
-def test_config2_d3q7_fp32_256cube_full_size():
+def test_d3q7_fp32_256cube_tube_full_size():
     """256^3 closed tube, FP32, 20000 steps: every node against the oracle's
     one-cell-wide run (x-only data stays y/z-uniform in a closed box)."""
     D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
@@ -183,7 +183,7 @@ def _window_oracle(lattice, D, x0, cx, cy, T):
     return x[:, 0, w // 2, w // 2]
 
 
-def test_config3_d2q9_fp32_2048_full_size():
+def test_d2q9_fp32_2048sq_n5_full_size():
     """2048^2 periodic D2Q9, N = 5, FP32: sampled nodes after 12 steps against the
     oracle on their dependency cones; mass, closure and flags after 10000 steps."""
     n = 5
