@@ -29,7 +29,7 @@ _LIB_PATH = os.path.join(_BUILD, "libmsoracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4}
+LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4, "D2Q4": 5, "D3Q6": 6}
 RELAX = {"magic": 0, "srt": 1, "frozen": 2}
 BC = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 

@@ -43,8 +43,8 @@
  * J_n = -sum_i J_i (Eq. 2-3a).
  *
  * Storage here is array-of-structures, f[cell][species][k], and the lattice
- * velocity order is the one printed in Eqs. 3-5, 3-7, 3-8, 3-10 and 3-11
- * (D1Q3, D2Q5, D2Q9, D3Q7, D3Q15).
+ * velocity order is the one printed in Eqs. 3-5 to 3-11 (D1Q3, D2Q4, D2Q5, D2Q9,
+ * D3Q6, D3Q7, D3Q15).
  *
  * Parity of every function is pinned by the CPU test-suite against closed forms
  * and printed numbers of the paper (Remarks I-IV, the D12 = D13 form of Sec. 4.2,
@@ -61,7 +61,8 @@
 #define ORC_MAXQ 15
 #define ORC_MAXN 8
 
-enum { ORC_D2Q5 = 0, ORC_D2Q9 = 1, ORC_D3Q7 = 2, ORC_D3Q15 = 3, ORC_D1Q3 = 4 };
+enum { ORC_D2Q5 = 0, ORC_D2Q9 = 1, ORC_D3Q7 = 2, ORC_D3Q15 = 3, ORC_D1Q3 = 4, ORC_D2Q4 = 5,
+       ORC_D3Q6 = 6 };
 enum { ORC_MAGIC = 0, ORC_SRT = 1, ORC_FROZEN = 2 };
 enum { ORC_PERIODIC = 0, ORC_NOFLUX = 1, ORC_DIRICHLET = 2 };
 enum { GRP_CONSERVED = 0, GRP_ODD = 1, GRP_EVEN = 2 };
@@ -168,6 +169,25 @@ static int lattice_init(int lat, orc_lattice* L)
             L->c[k][0] = cx[k];
             L->w[k] = (k == 0) ? 2.0 / 3.0 : 1.0 / 6.0;
         }
+    } else if (lat == ORC_D2Q4) {
+        /* Eq. 3-6: no rest velocity, w = 1/4. */
+        static const int cx[4] = {1, 0, -1, 0};
+        static const int cy[4] = {0, 1, 0, -1};
+        L->Q = 4; L->dim = 2;
+        for (int k = 0; k < 4; ++k) {
+            L->c[k][0] = cx[k]; L->c[k][1] = cy[k];
+            L->w[k] = 0.25;
+        }
+    } else if (lat == ORC_D3Q6) {
+        /* Eq. 3-9: no rest velocity, w = 1/6. */
+        static const int cx[6] = {1, -1, 0, 0, 0, 0};
+        static const int cy[6] = {0, 0, 1, -1, 0, 0};
+        static const int cz[6] = {0, 0, 0, 0, 1, -1};
+        L->Q = 6; L->dim = 3;
+        for (int k = 0; k < 6; ++k) {
+            L->c[k][0] = cx[k]; L->c[k][1] = cy[k]; L->c[k][2] = cz[k];
+            L->w[k] = 1.0 / 6.0;
+        }
     } else {
         return -1;
     }
@@ -234,11 +254,25 @@ static int lattice_init(int lat, orc_lattice* L)
             L->M[12][k] = y * z;
             L->M[13][k] = x * z;
             L->M[14][k] = x * y * z;
-        } else {
+        } else if (lat == ORC_D1Q3) {
             /* D1Q3: density, momentum, energy. */
             L->M[0][k] = 1.0;
             L->M[1][k] = x;
             L->M[2][k] = 3.0 * x * x - 2.0;
+        } else if (lat == ORC_D2Q4) {
+            /* D2Q4: density, two momenta, one normal-stress difference. */
+            L->M[0][k] = 1.0;
+            L->M[1][k] = x;
+            L->M[2][k] = y;
+            L->M[3][k] = x * x - y * y;
+        } else {
+            /* D3Q6: density, three momenta, two normal-stress differences. */
+            L->M[0][k] = 1.0;
+            L->M[1][k] = x;
+            L->M[2][k] = y;
+            L->M[3][k] = z;
+            L->M[4][k] = 2.0 * x * x - y * y - z * z;
+            L->M[5][k] = y * y - z * z;
         }
     }
     if (lat == ORC_D2Q5) {
@@ -256,8 +290,14 @@ static int lattice_init(int lat, orc_lattice* L)
                      GRP_ODD, GRP_ODD, GRP_EVEN, GRP_EVEN, GRP_EVEN, GRP_EVEN, GRP_EVEN,
                      GRP_ODD};
         memcpy(L->group, g, sizeof(g));
-    } else {
+    } else if (lat == ORC_D1Q3) {
         int g[3] = {GRP_CONSERVED, GRP_ODD, GRP_EVEN};
+        memcpy(L->group, g, sizeof(g));
+    } else if (lat == ORC_D2Q4) {
+        int g[4] = {GRP_CONSERVED, GRP_ODD, GRP_ODD, GRP_EVEN};
+        memcpy(L->group, g, sizeof(g));
+    } else {
+        int g[6] = {GRP_CONSERVED, GRP_ODD, GRP_ODD, GRP_ODD, GRP_EVEN, GRP_EVEN};
         memcpy(L->group, g, sizeof(g));
     }
     /* M^{-1} by numerical inversion of the packed Q x Q matrix. */

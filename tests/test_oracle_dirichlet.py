@@ -87,7 +87,8 @@ def test_second_order_convergence(lam1):
 
 @pytest.mark.parametrize("lat,shape", [("D2Q5", (1, 3, 16)), ("D2Q9", (1, 3, 16)),
                                        ("D3Q7", (2, 2, 16)), ("D3Q15", (2, 2, 16)),
-                                       ("D1Q3", (1, 1, 16))])
+                                       ("D1Q3", (1, 1, 16)), ("D2Q4", (1, 3, 16)),
+                                       ("D3Q6", (2, 2, 16))])
 @pytest.mark.parametrize("relax", ["magic", "srt"])
 def test_binary_linear_steady_state_is_exact(lat, shape, relax):
     o = _oracle()

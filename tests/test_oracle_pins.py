@@ -21,7 +21,7 @@ import theory as th
 
 pytestmark = pytest.mark.usefixtures("oracle_lib")
 
-LATTICES = ["D2Q5", "D2Q9", "D3Q7", "D3Q15", "D1Q3"]
+LATTICES = ["D2Q5", "D2Q9", "D3Q7", "D3Q15", "D1Q3", "D2Q4", "D3Q6"]
 
 
 def _oracle():
@@ -251,6 +251,8 @@ CASES = [
     ("D3Q15", (6, 5, 4), (1, 2, 1)),
     ("D3Q15", (9, 1, 1), (2, 0, 0)),
     ("D1Q3", (24, 1, 1), (3, 0, 0)),
+    ("D2Q4", (14, 10, 1), (1, 2, 0)),
+    ("D3Q6", (7, 6, 5), (1, 1, 1)),
 ]
 
 
@@ -295,9 +297,9 @@ def test_ternary_linear_response_exact(lat):
     c, w = th.golden_lattice(lat)
     cs2 = th.cs2_of(c, w)
     dims = {"D2Q5": (16, 6, 1), "D2Q9": (12, 8, 1), "D3Q7": (8, 4, 6), "D3Q15": (6, 4, 5),
-            "D1Q3": (16, 1, 1)}[lat]
+            "D1Q3": (16, 1, 1), "D2Q4": (12, 6, 1), "D3Q6": (8, 4, 6)}[lat]
     k = {"D2Q5": (1, 1, 0), "D2Q9": (1, 1, 0), "D3Q7": (1, 0, 1), "D3Q15": (1, 1, 1),
-         "D1Q3": (1, 0, 0)}[lat]
+         "D1Q3": (1, 0, 0), "D2Q4": (1, 1, 0), "D3Q6": (1, 0, 1)}[lat]
     nx, ny, nz = dims
     shape = (nz, ny, nx)
     D12, D13, D23 = 0.10, 0.08, 0.02
@@ -337,9 +339,9 @@ def test_frozen_mode_is_linear_and_exact(lat):
     c, w = th.golden_lattice(lat)
     cs2 = th.cs2_of(c, w)
     dims = {"D2Q5": (16, 6, 1), "D2Q9": (12, 8, 1), "D3Q7": (8, 4, 6), "D3Q15": (6, 4, 5),
-            "D1Q3": (16, 1, 1)}[lat]
+            "D1Q3": (16, 1, 1), "D2Q4": (12, 6, 1), "D3Q6": (8, 4, 6)}[lat]
     k = {"D2Q5": (1, 1, 0), "D2Q9": (1, 1, 0), "D3Q7": (1, 0, 1), "D3Q15": (1, 1, 1),
-         "D1Q3": (1, 0, 0)}[lat]
+         "D1Q3": (1, 0, 0), "D2Q4": (1, 1, 0), "D3Q6": (1, 0, 1)}[lat]
     nx, ny, nz = dims
     shape = (nz, ny, nx)
     D12, D13, D23 = 0.10, 0.08, 0.02
@@ -409,7 +411,7 @@ def test_ternary_continuum_decay():
 
 
 @pytest.mark.parametrize("lat,axis", [("D2Q5", 0), ("D2Q9", 1), ("D3Q7", 2), ("D3Q15", 1),
-                                      ("D1Q3", 0)])
+                                      ("D1Q3", 0), ("D2Q4", 1), ("D3Q6", 2)])
 def test_local_gradient_is_second_order(lat, axis):
     """Eq. xix: the gradient read from the first moments of the populations
     equals the spectral derivative of the mole-fraction field to O(dx^2)."""
@@ -463,12 +465,14 @@ def test_binary_flux_is_fick():
     ("D3Q7", ("noflux",) * 6),
     ("D3Q15", ("noflux", "noflux", "periodic", "periodic", "noflux", "noflux")),
     ("D1Q3", ("noflux", "noflux") + ("periodic",) * 4),
+    ("D2Q4", ("noflux",) * 4 + ("periodic",) * 2),
+    ("D3Q6", ("noflux",) * 6),
 ])
 def test_mass_conservation_and_closure(lat, bc):
     o = _oracle()
     n = 4
     D = sy.random_D(n, seed=43)
-    if lat in ("D3Q7", "D3Q15"):
+    if lat in ("D3Q7", "D3Q15", "D3Q6"):
         x0 = sy.sin_modes(n, 9, 7, 6, amp=0.1, seed=44)
     elif lat == "D1Q3":
         x0 = sy.sin_modes(n, 37, 1, amp=0.1, seed=46)
@@ -479,14 +483,14 @@ def test_mass_conservation_and_closure(lat, bc):
     np.testing.assert_allclose(x.sum(axis=0), 1.0, atol=1e-14)
 
 
-@pytest.mark.parametrize("lat", ["D2Q5", "D3Q7", "D1Q3"])
+@pytest.mark.parametrize("lat", ["D2Q5", "D3Q7", "D1Q3", "D2Q4", "D3Q6"])
 def test_bounce_back_equals_mirrored_periodic(lat):
     """Half-way bounce-back on [0, L) equals a periodic run of the mirrored field on
     [0, 2L) (exact for the axis-aligned lattices)."""
     o = _oracle()
     n = 3
     D = sy.D_from_pairs(3, {(1, 2): 0.1, (1, 3): 0.08, (2, 3): 0.02})
-    if lat == "D2Q5":
+    if lat in ("D2Q5", "D2Q4"):
         x0 = sy.sin_modes(n, 10, 7, amp=0.1, seed=47)
         axes = (3, 2)
     elif lat == "D1Q3":
