@@ -47,8 +47,18 @@ extern "C" {
 typedef struct lbms_s lbms_t;
 
 /* Lattices of Sec. 3.1: D2Q5 (Eq. 3-7), D2Q9 (Eq. 3-8), D3Q7 (Eq. 3-10),
- * D3Q15 (Eq. 3-11) and D1Q3 (Eq. 3-5).  Batched solves take the first three. */
-enum { LBMS_D2Q5 = 0, LBMS_D2Q9 = 1, LBMS_D3Q7 = 2, LBMS_D3Q15 = 3, LBMS_D1Q3 = 4 };
+ * D3Q15 (Eq. 3-11), D1Q3 (Eq. 3-5), and the two without a rest velocity, D2Q4
+ * (Eq. 3-6) and D3Q6 (Eq. 3-9).  Batched solves take the first three; the
+ * adjoint entry points all but D2Q4 and D3Q6. */
+enum {
+    LBMS_D2Q5 = 0,
+    LBMS_D2Q9 = 1,
+    LBMS_D3Q7 = 2,
+    LBMS_D3Q15 = 3,
+    LBMS_D1Q3 = 4,
+    LBMS_D2Q4 = 5,
+    LBMS_D3Q6 = 6
+};
 
 /* Storage and arithmetic type of the populations and of all fields. */
 enum { LBMS_F32 = 0, LBMS_F64 = 1 };
@@ -104,8 +114,8 @@ size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dt
 /*
  * Create a solver handle.
  *   out        receives the handle (set to NULL on failure).
- *   lattice    LBMS_D2Q5 | LBMS_D2Q9 | LBMS_D3Q7 | LBMS_D3Q15 | LBMS_D1Q3
- *              (Sec. 3.1).
+ *   lattice    LBMS_D2Q5 | LBMS_D2Q9 | LBMS_D3Q7 | LBMS_D3Q15 | LBMS_D1Q3 |
+ *              LBMS_D2Q4 | LBMS_D3Q6 (Sec. 3.1).
  *   n_species  n, 2..8.  S = n - 1 species are evolved (Eq. 3-2, i <= n-1).
  *   grid       {nx, ny, nz}, each >= 1; nz must be 1 for 2D lattices and
  *              ny = nz = 1 for D1Q3; nx * ny * nz <= LBMS_MAX_CELLS.

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
             if (cy != 0) { off += h.oy[cy > 0 ? 0 : 1]; bounce |= h.by[cy > 0 ? 0 : 1]; }
             if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
             const uint32_t dst = bounce ? cell : (uint32_t)((int32_t)cell + off);
-            const size_t plane = (size_t)(bounce ? opp(k) : k) * p.g.cells;
+            const size_t plane = (size_t)(bounce ? opp<LAT>(k) : k) * p.g.cells;
             bool neg = false;
             if (k != 0 && h.dir) {
                 const int wf = link_wall<LAT>(k, h);

@@ -1,0 +1,11 @@
+// Kernel instantiations for the D2Q4 lattice (all S = 1..7, float and double).
+#include "kernels.cuh"
+
+namespace lbms {
+
+cudaError_t dispatch_d2q4(Op op, int dtype, const KArgs& a)
+{
+    return dispatch_lattice<LBMS_D2Q4>(op, dtype, a);
+}
+
+}  // namespace lbms

@@ -34,10 +34,18 @@ int lattice_q(int lat)
         case LBMS_D3Q7: return 7;
         case LBMS_D3Q15: return 15;
         case LBMS_D1Q3: return 3;
+        case LBMS_D2Q4: return 4;
+        case LBMS_D3Q6: return 6;
         default: return 0;
     }
 }
-int lattice_dim(int lat) { return lat == LBMS_D3Q7 || lat == LBMS_D3Q15 ? 3 : (lat == LBMS_D1Q3 ? 1 : 2); }
+int lattice_dim(int lat)
+{
+    return lat == LBMS_D3Q7 || lat == LBMS_D3Q15 || lat == LBMS_D3Q6 ? 3 : (lat == LBMS_D1Q3 ? 1 : 2);
+}
+
+// The adjoint kernels treat population 0 as a rest population.
+bool adjoint_lattice(int lat) { return lat != LBMS_D2Q4 && lat != LBMS_D3Q6; }
 
 struct Layout {
     size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_bound, off_staging,
@@ -234,7 +242,9 @@ cudaError_t dispatch(const lbms_t* h, Op op, const KArgs& a)
         case LBMS_D2Q9: return dispatch_d2q9(op, h->dtype, a);
         case LBMS_D3Q7: return dispatch_d3q7(op, h->dtype, a);
         case LBMS_D3Q15: return dispatch_d3q15(op, h->dtype, a);
-        default: return dispatch_d1q3(op, h->dtype, a);
+        case LBMS_D1Q3: return dispatch_d1q3(op, h->dtype, a);
+        case LBMS_D2Q4: return dispatch_d2q4(op, h->dtype, a);
+        default: return dispatch_d3q6(op, h->dtype, a);
     }
 }
 
@@ -245,7 +255,8 @@ cudaError_t adj_dispatch(const lbms_t* h, AdjOp op, const AArgs& a)
         case LBMS_D2Q9: return adj_dispatch_d2q9(op, h->dtype, a);
         case LBMS_D3Q7: return adj_dispatch_d3q7(op, h->dtype, a);
         case LBMS_D3Q15: return adj_dispatch_d3q15(op, h->dtype, a);
-        default: return adj_dispatch_d1q3(op, h->dtype, a);
+        case LBMS_D1Q3: return adj_dispatch_d1q3(op, h->dtype, a);
+        default: return cudaErrorInvalidValue;  // rejected by the entry points
     }
 }
 
@@ -764,7 +775,7 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
 
 size_t lbms_adjoint_scratch_size(const lbms_t* h)
 {
-    if (!h || h->S > 4 || h->relax == LBMS_RELAX_FROZEN) return 0;
+    if (!h || h->S > 4 || h->relax == LBMS_RELAX_FROZEN || !adjoint_lattice(h->lattice)) return 0;
     return (size_t)node_blocks(h->cells) * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
 }
 
@@ -773,6 +784,7 @@ int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
+    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!grad_x || !lam) return fail(h, LBMS_EINVAL, "grad_x and lam must not be NULL");
     AArgs a;
     a.k = base_args(h, h->stream);
@@ -787,6 +799,7 @@ int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* l
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
+    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!f_prev || !lam_in || !lam_out || !gacc)
         return fail(h, LBMS_EINVAL, "f_prev, lam_in, lam_out and gacc must not be NULL");
     if (lam_in == lam_out) return fail(h, LBMS_EINVAL, "lam_in and lam_out must be different buffers");
@@ -805,6 +818,7 @@ int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
+    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!lam0 || !grad_x0) return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must not be NULL");
     AArgs a;
     a.k = base_args(h, h->stream);
@@ -819,6 +833,7 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
     if (!h) return LBMS_EINVAL;
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
+    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!gacc || !dL_dD) return fail(h, LBMS_EINVAL, "gacc and dL_dD must not be NULL");
     const int np = h->n * (h->n - 1) / 2;
     double* slot = reinterpret_cast<double*>(reinterpret_cast<char*>(h->status) + 128);

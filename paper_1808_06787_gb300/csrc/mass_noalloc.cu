@@ -95,7 +95,9 @@ extern "C" int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], 
                     : lattice == LBMS_D2Q9 ? dispatch_d2q9(OP_MASS, dtype, a)
                     : lattice == LBMS_D3Q7 ? dispatch_d3q7(OP_MASS, dtype, a)
                     : lattice == LBMS_D3Q15 ? dispatch_d3q15(OP_MASS, dtype, a)
-                                            : dispatch_d1q3(OP_MASS, dtype, a);
+                    : lattice == LBMS_D1Q3 ? dispatch_d1q3(OP_MASS, dtype, a)
+                    : lattice == LBMS_D2Q4 ? dispatch_d2q4(OP_MASS, dtype, a)
+                                           : dispatch_d3q6(OP_MASS, dtype, a);
     if (e != cudaSuccess) return set_call_error(LBMS_ECUDA, "mass kernel: %s", cudaGetErrorString(e));
     const bool host_out = !is_device_ptr(mass_out);
     double* dst = host_out ? reinterpret_cast<double*>(static_cast<char*>(scratch) + kPartialBytes) : mass_out;

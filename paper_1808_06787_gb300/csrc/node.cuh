@@ -194,7 +194,7 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
     for (int i = 0; i < S; ++i) moved[i] = T(0);
 #pragma unroll
     for (int pr = 0; pr < L::NPAIR; ++pr) {
-        const int ka = 2 * pr + 1, kb = 2 * pr + 2;
+        const int ka = L::K0 + 2 * pr, kb = ka + 1;
         const T wp = T(L::w(ka));
         T sym[S], asym[S];
 #pragma unroll
@@ -212,12 +212,18 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
             }
             const T na = f[i][ka] - (ds + da);
             const T nb = f[i][kb] - (ds - da);
-            moved[i] += (f[i][ka] - na) + (f[i][kb] - nb);
-            f[i][ka] = na;
+            if (ka == 0) {
+                // no rest velocity: population 0 is the absorber below
+                moved[i] += f[i][kb] - nb;
+            } else {
+                moved[i] += (f[i][ka] - na) + (f[i][kb] - nb);
+                f[i][ka] = na;
+            }
             f[i][kb] = nb;
         }
     }
-    // rest population: f+_0 = f_0 + sum_{k != 0} (f_k - f+_k); one hash per
+    // population 0 (the rest population; on lattices without one, the first
+    // moving population): f+_0 = f_0 + sum_{k != 0} (f_k - f+_k); one hash per
     // node, and per species an odd multiple of it offset by a species constant
     // (a bijection of a uniform 32-bit number, so again uniform)
     const uint32_t hn = mix32(key);
@@ -334,13 +340,13 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
         if (cy != 0) { off += h.oy[cy > 0 ? 0 : 1]; bounce |= h.by[cy > 0 ? 0 : 1]; }
         if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
         const uint32_t src = bounce ? cell : (uint32_t)((int32_t)cell + off);
-        const size_t plane = (size_t)(bounce ? opp(k) : k) * g.cells;
+        const size_t plane = (size_t)(bounce ? opp<LAT>(k) : k) * g.cells;
 #pragma unroll
         for (int s = 0; s < S; ++s) f[s][k] = fin[(size_t)s * Q * g.cells + plane + src];
     }
     if (h.dir) {
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
+        for (int k = L::K0; k < Q; ++k) {
             const int wf = link_wall<LAT>(k, h);
             if (wf >= 0 && ((h.dir >> wf) & 1u)) {
 #pragma unroll
@@ -370,7 +376,7 @@ __device__ __forceinline__ void flux_and_gradient(const T (&f)[S][Lattice<LAT>::
         for (int a = 0; a < DIM; ++a) {
             T acc = T(0);
 #pragma unroll
-            for (int k = 1; k < Q; ++k) {
+            for (int k = 0; k < Q; ++k) {
                 const int c = a == 0 ? L::cx(k) : (a == 1 ? L::cy(k) : L::cz(k));
                 if (c == 1) acc += f[s][k];
                 if (c == -1) acc -= f[s][k];

@@ -22,9 +22,9 @@ import torch
 
 from . import build as _build
 
-LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4}
-DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q15": 3, "D1Q3": 1}
-Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7, "D3Q15": 15, "D1Q3": 3}
+LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4, "D2Q4": 5, "D3Q6": 6}
+DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q15": 3, "D1Q3": 1, "D2Q4": 2, "D3Q6": 3}
+Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7, "D3Q15": 15, "D1Q3": 3, "D2Q4": 4, "D3Q6": 6}
 RELAX = {"magic": 0, "srt": 1, "frozen": 2}
 FACE = {"periodic": 0, "noflux": 1, "dirichlet": 2}
 DTYPES = {torch.float32: 0, torch.float64: 1}

@@ -46,7 +46,8 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in p.EXPORTED, name
 
 
-@pytest.mark.parametrize("lat,q,dim", [(0, 5, 2), (1, 9, 2), (2, 7, 3), (3, 15, 3), (4, 3, 1)])
+@pytest.mark.parametrize("lat,q,dim", [(0, 5, 2), (1, 9, 2), (2, 7, 3), (3, 15, 3), (4, 3, 1),
+                                       (5, 4, 2), (6, 6, 3)])
 @pytest.mark.parametrize("n", [2, 3, 8])
 @pytest.mark.parametrize("dtype,es", [(0, 4), (1, 8)])
 def test_workspace_size(lib, lat, q, dim, n, dtype, es):
@@ -68,7 +69,7 @@ def test_workspace_size_rejects(lib):
     assert p.lbms_workspace_size(0, 9, (4, 4, 1), 0) == 0  # too many
     assert p.lbms_workspace_size(0, 3, (4, 4, 2), 0) == 0  # 2D lattice, nz > 1
     assert p.lbms_workspace_size(2, 3, (0, 4, 4), 0) == 0  # empty grid
-    assert p.lbms_workspace_size(5, 3, (4, 4, 4), 0) == 0  # unknown lattice
+    assert p.lbms_workspace_size(7, 3, (4, 4, 4), 0) == 0  # unknown lattice
     assert p.lbms_workspace_size(4, 3, (4, 2, 1), 0) == 0  # 1D lattice, ny > 1
     assert p.lbms_workspace_size(2, 3, (4, 4, 4), 2) == 0  # unknown dtype
     assert p.lbms_workspace_size(2, 3, (2048, 2048, 1024), 0) == 0  # beyond 2^31 cells

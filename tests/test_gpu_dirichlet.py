@@ -69,6 +69,8 @@ CASES = [
     ("D3Q7", 4, (9, 8, 10), (P, P, P, P, B, B)),
     ("D3Q15", 3, (9, 7, 6), (B, B, W, W, B, W)),
     ("D1Q3", 3, (40, 1, 1), (B, B, P, P, P, P)),
+    ("D2Q4", 3, (22, 15, 1), (B, W, B, B, P, P)),
+    ("D3Q6", 3, (9, 8, 7), (B, B, W, W, B, W)),
 ]
 
 
@@ -177,7 +179,8 @@ def test_second_order_convergence_on_the_gpu():
 
 @pytest.mark.parametrize("lattice,dims", [("D2Q5", (16, 3, 1)), ("D2Q9", (16, 3, 1)),
                                           ("D3Q7", (16, 2, 2)), ("D3Q15", (16, 2, 2)),
-                                          ("D1Q3", (16, 1, 1))])
+                                          ("D1Q3", (16, 1, 1)), ("D2Q4", (16, 3, 1)),
+                                          ("D3Q6", (16, 2, 2))])
 def test_linear_steady_state_and_stream_ordered_boundary_change(lattice, dims):
     from paper_1808_06787_gb300 import Solver
 

@@ -78,6 +78,10 @@ SMALL = [
     ("D3Q15", 2, (6, 5, 4), (W, W, W, W, W, W)),
     ("D1Q3", 4, (53, 1, 1), (W, W, P, P, P, P)),
     ("D1Q3", 8, (40, 1, 1), (P, P, P, P, P, P)),
+    ("D2Q4", 3, (23, 17, 1), (W, W, P, P, P, P)),
+    ("D2Q4", 6, (15, 12, 1), (P, P, P, P, P, P)),
+    ("D3Q6", 3, (11, 9, 7), (W, W, W, W, W, W)),
+    ("D3Q6", 4, (8, 7, 6), (P, P, W, W, P, P)),
 ]
 
 
@@ -330,7 +334,7 @@ TOL_G = {torch.float64: 1e-11, torch.float32: 1e-4}
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
-@pytest.mark.parametrize("case", SMALL[:9] + SMALL[11:14], ids=lambda c: "%s-n%d-%dx%dx%d" % ((c[0], c[1]) + c[2]))
+@pytest.mark.parametrize("case", SMALL[:9] + SMALL[11:14] + SMALL[16:], ids=lambda c: "%s-n%d-%dx%dx%d" % ((c[0], c[1]) + c[2]))
 def test_gradient_parity(case, dtype):
     import oracle
 
@@ -424,6 +428,8 @@ FROZEN_CASES = [
     ("D3Q7", 3, (11, 9, 7), (W, W, P, P, W, W)),
     ("D3Q15", 3, (8, 7, 6), (P, P, P, P, P, P)),
     ("D1Q3", 5, (41, 1, 1), (W, W, P, P, P, P)),
+    ("D2Q4", 3, (20, 14, 1), (W, W, P, P, P, P)),
+    ("D3Q6", 3, (9, 8, 7), (P, P, P, P, W, W)),
 ]
 
 
@@ -458,3 +464,15 @@ def test_frozen_mode_parity(case, dtype):
     assert s.adjoint_scratch is not None
     with pytest.raises(LbmsError, match="adjoint"):
         s.adjoint_scratch()
+
+
+@pytest.mark.parametrize("lattice,dims", [("D2Q4", (12, 10, 1)), ("D3Q6", (8, 7, 6))])
+def test_adjoint_rejects_lattices_without_rest(lattice, dims):
+    from paper_1808_06787_gb300 import LbmsError, Solver
+
+    s = Solver(lattice, sy.random_D(3, seed=5), dims, dtype=torch.float64)
+    with pytest.raises(LbmsError, match="adjoint"):
+        s.adjoint_scratch()
+    lam = torch.zeros(s.state_shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(LbmsError, match="D2Q4 or D3Q6"):
+        s.adjoint_seed(torch.zeros(s.field_shape, dtype=torch.float64, device="cuda"), lam)
