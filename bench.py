@@ -81,7 +81,7 @@ class Workload:
         import synthetic as sy
 
         nx, ny, nz = grid or self.grid
-        if self.key in ("tube", "tube15", "line"):
+        if self.key in ("tube", "tube15", "tube6", "plane4", "line"):
             return sy.two_bulb(nx, ny, nz, width=4.0)
         if self.key == "blobs":
             return sy.gaussian_blobs(self.n, nx, ny, seed=1003)
@@ -90,7 +90,7 @@ class Workload:
     def sample_grid(self, cells_target: int):
         """A block of the workload with about cells_target nodes (oracle timing)."""
         nx, ny, nz = self.grid
-        if self.key in ("tube", "tube15"):  # x-slab of the closed tube: same physics per node
+        if self.key in ("tube", "tube15", "tube6"):  # x-slab of the closed tube: same physics per node
             sy_ = max(1, min(ny, cells_target // nx))
             sz = max(1, min(nz, cells_target // (nx * sy_)))
             return (nx, sy_, sz)
@@ -120,6 +120,18 @@ def make_workload(key: str, grid_edge: int) -> Workload:
                         "D3Q15 %d^3 ternary two-bulb closed tube, FP32, D = (0.10, 0.08, 0.02), "
                         "no-flux walls" % grid_edge,
                         "traffic_d3q15_256cube_f32.json")
+    if key == "tube6":
+        g = (grid_edge, grid_edge, grid_edge)
+        return Workload("tube6", "D3Q6", 6, g, 3, False, (W,) * 6,
+                        "D3Q6 %d^3 ternary two-bulb closed tube, FP32, D = (0.10, 0.08, 0.02), "
+                        "no-flux walls" % grid_edge,
+                        "traffic_d3q6_256cube_f32.json")
+    if key == "plane4":
+        e = 8192 if grid_edge == 256 else grid_edge
+        return Workload("plane4", "D2Q4", 4, (e, e, 1), 3, False, (W, W, P, P, P, P),
+                        "D2Q4 %d^2 ternary two-bulb, FP32, D = (0.10, 0.08, 0.02), no-flux x "
+                        "faces, periodic y" % e,
+                        "traffic_d2q4_8192sq_f32.json")
     if key == "line":
         nx = 1 << 26 if grid_edge == 256 else grid_edge
         return Workload("line", "D1Q3", 3, (nx, 1, 1), 3, False, (W, W, P, P, P, P),
@@ -363,6 +375,8 @@ def run_ours(args, wl: Workload):
         "dtype": "f64" if wl.f64 else "f32",
         "data": "synthetic (seeded %s; no dataset)" % {"tube": "two-bulb tanh profile",
                                                       "tube15": "two-bulb tanh profile",
+                                                      "tube6": "two-bulb tanh profile",
+                                                      "plane4": "two-bulb tanh profile",
                                                       "line": "two-bulb tanh profile",
                                                       "blobs": "Gaussian blobs",
                                                       "sine": "sine modes"}[wl.key],
@@ -371,6 +385,7 @@ def run_ours(args, wl: Workload):
             "lattice": wl.lattice, "grid": list(wl.grid), "n_species": wl.n,
             "evolved_species": wl.S,
             "bc": {"tube": "no-flux all faces", "tube15": "no-flux all faces",
+                   "tube6": "no-flux all faces", "plane4": "no-flux x, periodic y",
                    "line": "no-flux ends"}.get(wl.key, "periodic"),
             "relax": "MRT, Lambda_2 by Eq. 3-16",
             "glups_n_counted": round(glups * wl.n / wl.S, 4),
@@ -774,8 +789,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["tube", "blobs", "sine", "tube15", "line", "batch",
-                                           "adjoint"],
+    ap.add_argument("--workload", choices=["tube", "blobs", "sine", "tube15", "tube6", "plane4",
+                                           "line", "batch", "adjoint"],
                     default="tube")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the CPU baseline sample")
