@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
     using IO = LamIO<T>;
     constexpr int Q = L::Q;
     constexpr int NP = NPairs<S>::value;
+    await_previous_grid();
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
     const bool active = cell < p.g.cells;
     T dc[NP];
@@ -450,8 +451,7 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
         p.relax = a.k.relax;
         p.xb = static_cast<const T*>(a.k.xb);
         p.co = make_coeffs<T>(a.k);
-        k_adjoint_step<LAT, S, T><<<blocks, kBlock, 0, a.k.stream>>>(p);
-        return cudaGetLastError();
+        return launch_chained(k_adjoint_step<LAT, S, T>, blocks, kBlock, a.k.stream, p);
     }
     AdjFieldParams<T> p;
     p.grad_x = static_cast<const T*>(a.grad_x);

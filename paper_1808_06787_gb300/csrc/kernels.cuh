@@ -51,6 +51,40 @@ struct StepParams {
     Coeffs<T> co;
 };
 
+// Programmatic dependent launch (sm_90 and later).  Time steps are launched
+// with programmatic stream serialisation (launch_chained below), so the blocks
+// of the next step may be made resident while the current one still runs and
+// its launch latency is hidden.  Every thread first waits here until the grid
+// before it in the stream has completed and its stores are visible (a wait the
+// hardware resolves, not a spin on memory), then lets the following grid be
+// scheduled.  In a grid launched without the attribute both return at once.
+__device__ __forceinline__ void await_previous_grid()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches `kernel` with programmatic stream serialisation: only the
+// dependency on the kernel before it in the stream is relaxed, and the kernel
+// must call await_previous_grid before touching memory that grid writes or reads.
+template <typename... Params, typename... Args>
+cudaError_t launch_chained(void (*kernel)(Params...), uint32_t blocks, uint32_t threads,
+                           cudaStream_t stream, Args... args)
+{
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+    return cudaGetLastError();
+}
+
 // Raise the status flags for mole fractions that are non-finite or far
 // outside [0, 1]; the comparison is false for NaN, so one test covers both.
 template <int S, typename T>
@@ -161,6 +195,7 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
+    await_previous_grid();
     const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = cell < p.g.cells;
     const uint32_t step = *p.clock_in;
@@ -361,12 +396,9 @@ cudaError_t launch(Op op, const KArgs& a)
         p.co = make_coeffs<T>(a);
         const uint32_t tb = a.step_block;
         const uint32_t blocks = (a.cells + tb - 1) / tb;
-        if (op == OP_STEP)
-            k_step<LAT, S, T, false><<<blocks, tb, 0, a.stream>>>(p);
-        else if (op == OP_STEP_MASS)
-            k_step<LAT, S, T, true><<<blocks, tb, 0, a.stream>>>(p);
-        else
-            k_mass<LAT, S, T><<<blocks, tb, 0, a.stream>>>(p);
+        if (op == OP_STEP) return launch_chained(k_step<LAT, S, T, false>, blocks, tb, a.stream, p);
+        if (op == OP_STEP_MASS) return launch_chained(k_step<LAT, S, T, true>, blocks, tb, a.stream, p);
+        k_mass<LAT, S, T><<<blocks, tb, 0, a.stream>>>(p);
         return cudaGetLastError();
     }
     FieldParams<T> p;
