@@ -422,6 +422,51 @@ def test_d1q3_line_full_size_window():
     assert s.status() == 0
 
 
+def test_d3q6_tube_full_size_window():
+    """D3Q6 256^3 closed ternary tube (bench workload `tube6`, no rest velocity),
+    FP32: the interface region after T steps against the oracle on an x-window of
+    the full y-z cross-section (a node depends only on nodes within T cells), and mass."""
+    from paper_1808_06787_gb300 import Solver
+    import oracle
+
+    D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
+    N, T, half = 256, 24, 40
+    s = Solver("D3Q6", D, (N, N, N), bc="noflux", dtype=torch.float32)
+    x0 = sy.two_bulb(N, N, N, width=4.0)
+    s.set_state(torch.from_numpy(x0).float().cuda())
+    m0 = s.mass()
+    s.step(T)
+    x = s.moments()[:, :, :, N // 2 - 8:N // 2 + 8].double().cpu().numpy()
+    win = x0[:, :, :, N // 2 - half:N // 2 + half]
+    ref = oracle.run("D3Q6", D, win, T, bc=("noflux",) * 6)[:, :, :, half - 8:half + 8]
+    assert np.abs(x - ref).max() <= 2e-5
+    assert np.all(np.abs(s.mass() - m0) <= 1e-6 * np.abs(m0))
+    assert s.status() == 0
+
+
+def test_d2q4_plane_full_size_window():
+    """D2Q4 8192^2 ternary two-bulb plane (bench workload `plane4`, no rest velocity;
+    no-flux x faces, periodic y), FP32: the interface region after T steps against
+    the oracle on an x-window of all 8192 rows, and mass."""
+    from paper_1808_06787_gb300 import Solver
+    import oracle
+
+    D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
+    N, T, half = 8192, 24, 40
+    bc = ("noflux", "noflux") + ("periodic",) * 4
+    s = Solver("D2Q4", D, (N, N, 1), bc=bc, dtype=torch.float32)
+    x0 = sy.two_bulb(N, N, 1, width=4.0)
+    s.set_state(torch.from_numpy(x0).float().cuda())
+    m0 = s.mass()
+    s.step(T)
+    x = s.moments()[:, :, :, N // 2 - 8:N // 2 + 8].double().cpu().numpy()
+    win = x0[:, :, :, N // 2 - half:N // 2 + half]
+    ref = oracle.run("D2Q4", D, win, T, bc=bc)[:, :, :, half - 8:half + 8]
+    assert np.abs(x - ref).max() <= 2e-5
+    assert np.all(np.abs(s.mass() - m0) <= 1e-6 * np.abs(m0))
+    assert s.status() == 0
+
+
 FROZEN_CASES = [
     ("D2Q5", 3, (24, 18, 1), (P, P, W, W, P, P)),
     ("D2Q9", 4, (17, 13, 1), (P, P, P, P, P, P)),
