@@ -327,14 +327,17 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
     using IO = LamIO<T>;
     constexpr int Q = L::Q;
     constexpr int NP = NPairs<S>::value;
-    await_previous_grid();
     const uint32_t cell = blockIdx.x * kBlock + threadIdx.x;
     const bool active = cell < p.g.cells;
+    // the gather and scatter offsets depend on the geometry only: formed while
+    // the previous step drains
+    Neighbourhood h;
+    if (active) h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
+    await_previous_grid();
     T dc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) dc[q] = T(0);
     if (active) {
-        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
         T f[S][Q], d[S][Q], mud[S][Q], lbar[S];
         pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
 #pragma unroll
