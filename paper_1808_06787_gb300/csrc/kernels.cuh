@@ -54,10 +54,11 @@ struct StepParams {
 // Programmatic dependent launch (sm_90 and later).  Time steps are launched
 // with programmatic stream serialisation (launch_chained below), so the blocks
 // of the next step may be made resident while the current one still runs and
-// its launch latency is hidden.  Every thread first waits here until the grid
-// before it in the stream has completed and its stores are visible (a wait the
-// hardware resolves, not a spin on memory), then lets the following grid be
-// scheduled.  In a grid launched without the attribute both return at once.
+// its launch latency is hidden.  Before touching memory, every thread waits
+// here until the grid before it in the stream has completed and its stores are
+// visible (a wait the hardware resolves, not a spin on memory), then lets the
+// following grid be scheduled.  Arithmetic on the launch parameters alone may
+// come first.  In a grid launched without the attribute both return at once.
 __device__ __forceinline__ void await_previous_grid()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
