@@ -241,8 +241,10 @@ int lbms_mass(lbms_t* h, double* mass_out);
  *   cuda_stream  stream the work is ordered on; a host mass_out synchronises it.
  * The per-block partial sums go to a file-scope device array of 4 MiB that
  * every GPU which loads the library keeps until the process exits; grids whose
- * partials do not fit (cells * n_species * 8 bytes for F32, * 16 for F64, above
- * 4 MiB - 256 B, i.e. about 67 M node-species in F32) are rejected with
+ * partials do not fit (one record per block of 256 nodes -- of 64 nodes below
+ * 77824 nodes, as a solver's mass kernel uses -- and species, 8 bytes for F32
+ * and 16 for F64, above 4 MiB - 256 B: about 134 M node-species in F32 and
+ * 67 M in F64) are rejected with
  * LBMS_EINVAL and a message in lbms_last_error(NULL).  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  All calls

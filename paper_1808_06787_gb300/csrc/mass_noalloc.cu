@@ -71,7 +71,9 @@ extern "C" int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], 
         return set_call_error(LBMS_EINVAL, "invalid lattice/species/grid/dtype combination");
     if (!populations || !mass_out) return set_call_error(LBMS_EINVAL, "populations and mass_out must not be NULL");
     const uint32_t cells = (uint32_t)((size_t)grid[0] * grid[1] * grid[2]);
-    const uint32_t blocks = node_blocks(cells);
+    // the block partition of a solver's own mass kernel, so that both entry
+    // points run the same reduction (the FP64 compensated sums depend on it)
+    const uint32_t blocks = step_blocks(cells);
     const size_t record = dtype == LBMS_F64 ? 16 : 8;
     const size_t need = (size_t)blocks * n_species * record;
     if (need > kPartialBytes)
@@ -86,6 +88,7 @@ extern "C" int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], 
     KArgs a;
     a.nx = grid[0]; a.ny = grid[1]; a.nz = grid[2];
     a.cells = cells;
+    a.step_block = step_block_for(cells);
     a.n_species = n_species;
     a.fout = const_cast<void*>(populations);  // read only by the mass kernel
     a.partials = scratch;

@@ -81,3 +81,30 @@ def test_noalloc_matches_lbms_mass_twice(dtype):
     assert rc == 0
     torch.cuda.synchronize()
     assert np.array_equal(dev.cpu().numpy(), outs[0])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("dims", [(1, 1, 1), (24, 20, 10), (64, 64, 18), (64, 64, 19)],
+                         ids=["1node", "small", "below-77824", "at-77824"])
+def test_noalloc_bit_identical_to_lbms_mass_at_every_size(dims, dtype):
+    """Right after set_state both entry points reduce the same populations with
+    the same block partition (64-node blocks below 77824 nodes, 256 above), so
+    the results agree bit for bit, FP64 compensated sums included."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1808_06787_gb300 as p
+    from paper_1808_06787_gb300 import Solver
+
+    lib = p.load()
+    D = sy.D_from_pairs(3, {(1, 2): 0.10, (1, 3): 0.08, (2, 3): 0.02})
+    x0 = sy.sin_modes(3, *dims, amp=0.1, seed=11) if dims[2] == 1 else sy.two_bulb(*dims)
+    s = Solver("D3Q7", D, dims, bc="noflux", dtype=dtype)
+    s.set_state(torch.from_numpy(x0).to(dtype).cuda())
+    ref = s.mass()
+    out = np.full(3, np.nan)
+    rc = _call(lib, 2, 3, dims, 1 if dtype == torch.float64 else 0, s.populations().data_ptr(),
+               out.ctypes.data_as(ctypes.c_void_p))
+    assert rc == 0, lib.lbms_last_error(None).decode()
+    assert np.array_equal(out, ref), (out, ref)
+    s.close()
