@@ -126,3 +126,39 @@ def test_null_handle_calls(lib):
     assert lib.lbms_steps_done(None) == -1
     assert lib.lbms_populations(None) is None
     lib.lbms_destroy(None)
+
+
+def _header_enums():
+    """NAME = value pairs of the enums and #defines of include/lbms.h."""
+    text = open(os.path.join(ROOT, "include", "lbms.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    vals = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, v in re.findall(r"(LBMS_\w+)\s*=\s*(\d+)", body):
+            vals[name] = int(v)
+    for name, v in re.findall(r"#define\s+(LBMS_\w+)\s+(0x[0-9a-fA-F]+|\d+)", text):
+        vals[name] = int(v, 0)
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding passes the header's enum values, not its own."""
+    import paper_1808_06787_gb300.lbms as b
+
+    h = _header_enums()
+    for name, v in b.LATTICES.items():
+        assert h["LBMS_" + name] == v, name
+    assert {"magic": h["LBMS_RELAX_MAGIC"], "srt": h["LBMS_RELAX_SRT"],
+            "frozen": h["LBMS_RELAX_FROZEN"]} == b.RELAX
+    assert {"periodic": h["LBMS_PERIODIC"], "noflux": h["LBMS_NOFLUX"],
+            "dirichlet": h["LBMS_DIRICHLET"]} == b.FACE
+    assert sorted(b.DTYPES.values()) == [h["LBMS_F32"], h["LBMS_F64"]]
+    assert b.FLAG_NONFINITE == h["LBMS_FLAG_NONFINITE"]
+    assert b.FLAG_RANGE == h["LBMS_FLAG_RANGE"]
+    assert b.FLAG_INIT == h["LBMS_FLAG_INIT"]
+    assert b.BATCH_CANDIDATES == h["LBMS_BATCH_CANDIDATES"]
+    codes = {v: k[len("LBMS_"):] for k, v in h.items()
+             if k in ("LBMS_EINVAL", "LBMS_ENOMEM", "LBMS_ECUDA", "LBMS_ENONFINITE", "LBMS_ERANGE",
+                      "LBMS_ETIMEOUT")}
+    assert codes == b.ERRORS
+    assert b.LBMS_OK == h["LBMS_OK"] == 0
