@@ -14,8 +14,9 @@
  *   3. D~ = B^{-1} (Eq. 2-11) by Gauss-Jordan elimination with partial pivoting.
  *   4. Lambda_1 from the Chapman-Enskog relation D~ = c_s^2 (Lambda_1^{-1} - I/2)
  *      (Eq. 3-26), i.e. Lambda_1 = (D~ / c_s^2 + I/2)^{-1}, a second explicit
- *      inverse.  c_s^2 = sum_k w_k c_kx^2 of the lattice (1/3 for D2Q5 and D2Q9,
- *      1/4 for D3Q7; the paper derives Eq. 3-26 for D2Q5 only).
+ *      inverse.  c_s^2 = sum_k w_k c_kx^2 of the lattice (1/3 for D1Q3, D2Q5,
+ *      D2Q9, D3Q6 and D3Q15, 1/4 for D3Q7, 1/2 for D2Q4; the paper derives
+ *      Eq. 3-26 for D2Q5 only).
  *   5. Lambda_2 by Eq. 3-16 (off-diagonal = Lambda_1, diagonal
  *      8 (l - 2) / (l - 8)); or Lambda_2 = Lambda_1 in the single-relaxation-time
  *      reduction; lambda_0 = 1 (Sec. 3.1).  A third, frozen mode evaluates steps
