@@ -1,22 +1,27 @@
 """Throughput of the fused Maxwell-Stefan MRT stream-collide on GB300.
 
-Default workload (--workload tube): ternary two-bulb (Loschmidt-like)
-diffusion on D3Q7, 256^3 nodes, FP32, no-flux bounce-back walls on all six
-faces, left half x = (0, 0.5, 0.5), right half x = (0.5, 0.5, 0) joined by a
-tanh interface of width 4 cells, D12 : D13 : D23 = 5 : 4 : 1 scaled to max
-lattice D = 0.1.  Other workloads (for measurement of the other
-configurations): --workload blobs (D2Q9, 2048^2, 5 species, FP32, periodic,
-seeded Gaussian blobs, D_ij uniform in [0.01, 0.12]) and --workload sine
-(D2Q5, 128^2, ternary, FP64, periodic, seeded sine modes).
+Headline workload (--workload tube, the default): ternary two-bulb
+(Loschmidt-like) diffusion on D3Q7, 256^3 nodes, FP32, no-flux bounce-back
+walls on all six faces, left half x = (0, 0.5, 0.5), right half
+x = (0.5, 0.5, 0) joined by a tanh interface of width 4 cells,
+D12 : D13 : D23 = 5 : 4 : 1 scaled to max lattice D = 0.1.
 
 One bench step is one lattice Boltzmann time step of the whole grid: pull
 streaming with the boundary faces, mole fractions, the per-node
 Maxwell-Stefan relaxation matrices, collision and store (the last step of
-the timed run also writes the per-species mass partials and reduces them).
+each timed region also writes the per-species mass partials).  The timed
+region is --steps steps, bracketed by barrier + synchronize and timed with
+CUDA events on the launching stream; it is repeated until about a second
+has been timed and the median is reported.
 
 Metric: GLUPS = evolved-species node updates per second, S * cells * steps / s
 with S = n - 1 distributions per node (the n-th species follows from the
-closure); the n-counted figure is reported beside it.
+closure); the n-counted figure is reported beside it.  The rest of the
+metric is timed in the same run, at the same --steps, under "workloads":
+five species on D2Q9 2048^2 (blobs), the FP64 D2Q5 128^2 run (sine), the
+4096 batched solves (solves/s) and the adjoint/forward cost of the 512^2
+gradient (at its own 4000 steps).  --workload selects another headline
+(also D3Q15, D3Q6, D2Q4 and D1Q3 workloads) and --no-extras skips the rest.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
@@ -39,7 +44,7 @@ from dataclasses import dataclass
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "GLUPS (species-node updates/s) and % of HBM roofline"
+METRIC = "GLUPS (species-node updates/s) and % of HBM roofline; batched solves/s; adjoint/fwd cost"
 KERNEL_SOURCES = sorted(
     os.path.relpath(p_, os.path.dirname(os.path.abspath(__file__)))
     for p_ in glob.glob(os.path.join(os.path.dirname(os.path.abspath(__file__)),
@@ -236,25 +241,33 @@ class ClockSampler:
 
 
 # FP64 work of the D2Q5 ternary step per node, counted by ncu on the kernel
-# (DADD + DMUL + 2 DFMA: 59 + 26 + 2 x 43 per node); GB300 issues 2 DFMA per SM
-# and cycle (ncu's peak_sustained of 304 per cycle over 152 SMs).
+# (DADD + DMUL + 2 DFMA: 59 + 26 + 2 x 43 per node).  GB300 issues 2 DFMA per
+# SM and cycle (ncu's peak_sustained of 304 per cycle over its 152 SMs).
 D2Q5_TERNARY_FP64_FLOPS_PER_NODE = 171.0
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x 2 flops x max SM clock
+DFMA_PER_SM_CLK = 2
 
 
-def fp64_roofline(wl: "Workload", step_ms: float) -> dict:
+def fp64_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """FP64-pipe peak: SMs x DFMA per SM and clock x 2 flops x SM clock."""
+    return sms * DFMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp64_roofline(wl: "Workload", step_ms: float, sms: int, sm_mhz: float) -> dict:
     """ALU roofline of the L2-resident FP64 workload: its step kernel is bound by the
-    FP64 pipes (58 % of their issue slots busy under ncu), not by HBM."""
+    FP64 pipes (58 % of their issue slots busy under ncu), not by HBM.  The peak
+    uses the device's SM count and the SM clock sampled while it ran."""
     flops = D2Q5_TERNARY_FP64_FLOPS_PER_NODE * wl.cells
     achieved = flops / (step_ms * 1e-3) / 1e12
+    peak = fp64_peak_tflops(sms, sm_mhz)
     return {
         "bound": "alu",
         "achieved": round(achieved, 4),
-        "peak": round(FP64_PEAK_TFLOPS, 4),
+        "peak": round(peak, 4),
         "unit": "TFLOP/s",
-        "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+        "frac": round(achieved / peak, 4),
         "traffic": measured_traffic(wl),
-        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2070 MHz (FP64 pipe)",
+        "peak_source": "derived: %d SMs x %d DFMA/clk x 2 flops x %.0f MHz (sampled SM clock; FP64 pipe)"
+                       % (sms, DFMA_PER_SM_CLK, sm_mhz),
         "algorithmic_flops_per_launch": flops,
         "note": "FP64 flops per node counted by ncu on this kernel; state L2-resident",
     }
@@ -294,19 +307,43 @@ def job_rate(units_per_rank: float, world: int, t_ms: float) -> float:
     return units_per_rank * world / (t_ms * 1e-3)
 
 
-def run_ours(args, wl: Workload):
+MIN_TIMED_S = 1.0  # repeats of the K-step region fill at least this long (clock samples)
+MAX_REPEATS = 1000
+
+
+def timed_repeats(run_steps, stream, steps: int, barrier, min_repeats: int = 5):
+    """Device time of `steps` steps (CUDA events on the launching stream, barrier +
+    synchronize on both sides), repeated until at least MIN_TIMED_S has been spent
+    (and at least min_repeats times); returns (median ms, list of ms)."""
+    import torch
+
+    times = []
+    spent = 0.0
+    while len(times) < min_repeats or (spent < MIN_TIMED_S * 1e3 and len(times) < MAX_REPEATS):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        run_steps(steps)
+        ev1.record(stream)
+        barrier()
+        times.append(ev0.elapsed_time(ev1))
+        spent += times[-1]
+    return statistics.median(times), times
+
+
+def local_barrier():
+    import torch
+
+    torch.cuda.synchronize()
+
+
+def measure_single(wl: Workload, steps: int, warmup: int, barrier=local_barrier, keep=False):
+    """Time `steps` steps of a single-solve workload (inputs resident in HBM)."""
     import numpy as np
     import torch
 
     from paper_1808_06787_gb300 import Solver
-
-    world, rank, local, dist = dist_context()
-    torch.cuda.set_device(local)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
 
     tdtype = torch.float64 if wl.f64 else torch.float32
     x0_host = torch.from_numpy(wl.x0()).to(tdtype).pin_memory()
@@ -315,71 +352,51 @@ def run_ours(args, wl: Workload):
         s = Solver(wl.lattice, wl.D(), wl.grid, bc=wl.bc, dtype=tdtype, stream=stream)
         s.set_state(x0_host.cuda(non_blocking=True))
         mass0 = s.mass()
-        s.step(args.warmup)
+        s.step(warmup)
         torch.cuda.synchronize()
-
-        sampler = ClockSampler(local)
-        barrier()
-        sampler.start()
-        time.sleep(0.3)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        ev0.record(stream)
-        s.step(args.steps)
-        ev1.record(stream)
-        barrier()
-        ms = ev0.elapsed_time(ev1)
-        clocks = sampler.stop()
+        ms, reps = timed_repeats(s.step, stream, steps, barrier)
         flags = s.status()
         mass = s.mass()
+    out = {"ms": ms, "repeats_ms": reps, "status_flags": flags,
+           "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
+           "x0_host": x0_host, "stream": stream}
+    if keep:
+        out["solver"] = s
+    else:
+        s.close()
+    return out
 
-        # end to end through the public API with host buffers: pinned x0 in,
-        # K steps, mole fractions and masses back to pinned host memory
-        x_host = torch.empty(s.field_shape, dtype=tdtype).pin_memory()
-        e2e_s = None
-        if not args.no_e2e:
-            barrier()
-            t0 = time.perf_counter()
-            s.set_state(x0_host)
-            s.step(args.steps)
-            s.moments(x_host)
-            s.mass()
-            barrier()
-            e2e_s = time.perf_counter() - t0
 
-    e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
-    t_ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms])
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
-    cells = wl.cells
-    updates = float(wl.S) * cells * args.steps * world
-    glups = job_rate(float(wl.S) * cells * args.steps, world, t_ms) / 1e9
-    bytes_per_launch = 2.0 * wl.S * wl.Q * wl.es * cells
-    achieved = bytes_per_launch / (t_ms * 1e-3 / args.steps) / 1e9
+def hbm_roofline(bytes_per_launch: float, launch_ms: float, traffic) -> dict:
     peak, peak_kind = hbm_peak()
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    return {
+        "bound": "hbm",
+        "achieved": round(achieved, 1),
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": round(achieved / peak, 4),
+        "traffic": traffic,
+        "peak_source": peak_kind,
+        "algorithmic_bytes_per_launch": bytes_per_launch,
+    }
+
+
+def single_line(wl: Workload, m: dict, steps: int, world: int, t_ms: float, sms: int, sm_mhz: float):
+    """GLUPS, roofline and identification of a single-solve measurement."""
+    glups = job_rate(float(wl.S) * wl.cells * steps, world, t_ms) / 1e9
+    bytes_per_launch = 2.0 * wl.S * wl.Q * wl.es * wl.cells
     state_gb = bytes_per_launch / 1e9
-    out = {
-        "metric": METRIC,
+    roof = (fp64_roofline(wl, t_ms / steps, sms, sm_mhz) if wl.key == "sine"
+            else hbm_roofline(bytes_per_launch, t_ms / steps, measured_traffic(wl)))
+    return {
         "value": round(glups, 4),
         "unit": "GLUPS",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(t_ms / args.steps, 6),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
+        "steps": steps,
+        "ms_per_step": round(t_ms / steps, 6),
+        "repeats": len(m["repeats_ms"]),
+        "repeat_ms_min_max": [round(min(m["repeats_ms"]), 4), round(max(m["repeats_ms"]), 4)],
         "dtype": "f64" if wl.f64 else "f32",
-        "data": "synthetic (seeded %s; no dataset)" % {"tube": "two-bulb tanh profile",
-                                                      "tube15": "two-bulb tanh profile",
-                                                      "tube6": "two-bulb tanh profile",
-                                                      "plane4": "two-bulb tanh profile",
-                                                      "line": "two-bulb tanh profile",
-                                                      "blobs": "Gaussian blobs",
-                                                      "sine": "sine modes"}[wl.key],
         "config": {
             "workload": wl.description,
             "lattice": wl.lattice, "grid": list(wl.grid), "n_species": wl.n,
@@ -392,49 +409,22 @@ def run_ours(args, wl: Workload):
             "l2": ("state %.2f GB per step vs 129 MB L2; no flush" % state_gb) if state_gb > 0.5
             else ("state %.1f MB per step is L2-resident: L2/latency bound, not an HBM test"
                   % (state_gb * 1e3)),
-            "parallelism": "replicas" if world > 1 else "single GPU",
         },
-        "roofline": fp64_roofline(wl, t_ms / args.steps) if wl.key == "sine" else {
-            "bound": "hbm",
-            "achieved": round(achieved, 1),
-            "peak": peak,
-            "unit": "GB/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": measured_traffic(wl),
-            "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": bytes_per_launch,
-        },
-        "e2e": None if args.no_e2e else {
-            "value": round(updates / (e2e_ms * 1e-3) / 1e9, 4),
-            "unit": "GLUPS",
-            "h2d_bytes_per_step": round(x0_host.numel() * wl.es / args.steps, 1),
-            "d2h_bytes_per_step": round((x_host.numel() * wl.es + 8 * wl.n) / args.steps, 1),
-        },
-        "gpu_launches": args.steps + 1,
-        "clocks": clocks,
-        "status_flags": flags,
-        "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
+        "roofline": roof,
+        "gpu_launches": steps,
+        "status_flags": m["status_flags"],
+        "mass_drift_rel": m["mass_drift_rel"],
     }
-    if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
-    print(json.dumps(out))
-    if dist is not None:
-        dist.destroy_process_group()
 
 
-BATCH_COUNT = 4096
-BATCH_SOLVE_STEPS = 5000
-
-
-def run_batch(args):
-    """Batched workload: 4096 independent ternary D2Q5 FP32 solves, square sides uniform
-    in [32, 256], per-instance D_ij uniform in [0.01, 0.12], sine (periodic) or
-    two-bulb tanh (no-flux x) initial fields; schedule chosen by the tuner."""
-    import numpy as np
+def device_sms(local: int) -> int:
     import torch
 
-    import synthetic as sy
-    from paper_1808_06787_gb300 import BatchSolver
+    return int(torch.cuda.get_device_properties(local).multi_processor_count)
+
+
+def run_ours(args, wl: Workload):
+    import torch
 
     world, rank, local, dist = dist_context()
     torch.cuda.set_device(local)
@@ -444,128 +434,208 @@ def run_batch(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    count = BATCH_COUNT if args.grid == 256 else max(1, args.grid)
-    grids, Ds, bcs = sy.batch_instances(count, seed=1004 + rank)
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        b = BatchSolver("D2Q5", Ds, grids, bcs=bcs, dtype=torch.float32, stream=stream)
-        if args.batch_schedule < 0:
-            chosen, tune_ms = b.tune(trial_steps=16)
-        else:
-            b.set_schedule(args.batch_schedule)
-            chosen, tune_ms = args.batch_schedule, []
-        launches_per_step = b.launches_per_step()
-        x0_host = torch.empty(int(b.offsets[-1]), dtype=torch.float32).pin_memory()
-        for i in range(count):
-            x0_host[int(b.offsets[i]):int(b.offsets[i + 1])] = torch.from_numpy(
-                sy.batch_field(i, int(grids[i][0]), seed=1004 + rank).reshape(-1)).float()
-        b.set_state(x0_host.cuda(non_blocking=True))
-        mass0 = b.mass()
-        b.step(args.warmup)
-        sampler = ClockSampler(local)
-        barrier()
-        sampler.start()
-        time.sleep(0.3)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        barrier()
-        ev0.record(stream)
-        b.step(args.steps)
-        ev1.record(stream)
-        barrier()
-        ms = ev0.elapsed_time(ev1)
-        clocks = sampler.stop()
-        flags = b.status()
-        mass = b.mass()
-        e2e_s = None
-        if not args.no_e2e:
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    m = measure_single(wl, args.steps, args.warmup, barrier, keep=True)
+    clocks = sampler.stop()
+    s, stream, x0_host = m["solver"], m["stream"], m["x0_host"]
+    tdtype = x0_host.dtype
+
+    # end to end through the public API with host buffers: pinned x0 in,
+    # K steps, mole fractions and masses back to pinned host memory
+    x_host = torch.empty(s.field_shape, dtype=tdtype).pin_memory()
+    e2e_s = None
+    if not args.no_e2e:
+        with torch.cuda.stream(stream):
             barrier()
             t0 = time.perf_counter()
-            b.set_state(x0_host)
-            b.step(args.steps)
-            b.moments(out_device="cpu")
-            b.mass()
+            s.set_state(x0_host)
+            s.step(args.steps)
+            s.moments(x_host)
+            s.mass()
             barrier()
             e2e_s = time.perf_counter() - t0
+    s.close()
     e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
-    t_ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms])
+    t_ms, e2e_ms = max_over_ranks(dist, [m["ms"], e2e_ms])
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = measure_extras(args, wl, local)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    nodes = float(sum(int(g[0]) * int(g[1]) for g in grids))
-    solves = job_rate(count * args.steps / BATCH_SOLVE_STEPS, world, t_ms)
-    glups = 2.0 * nodes * world * args.steps / (t_ms * 1e-3) / 1e9
-    bytes_per_step = 2.0 * 2 * 5 * 4 * nodes
-    achieved = bytes_per_step / (t_ms * 1e-3 / args.steps) / 1e9
-    peak, peak_kind = hbm_peak()
+    sms = device_sms(local)
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    line = single_line(wl, m, args.steps, world, t_ms, sms, mhz)
+    updates = float(wl.S) * wl.cells * args.steps * world
     out = {
-        "metric": "batched solves/s (5000-step ternary D2Q5 solves) and GLUPS",
-        "value": round(solves, 3),
-        "unit": "solves/s",
+        "metric": METRIC,
+        "value": line["value"],
+        "unit": "GLUPS",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(t_ms / args.steps, 6),
+        "ms_per_step": line["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic (seeded sides, diffusivities, sine / tanh fields; no dataset)",
-        "config": {
-            "workload": "batched: %d ternary D2Q5 FP32 solves, sides uniform in [32, 256] "
-                        "(%.1f M nodes), D_ij uniform in [0.01, 0.12], sine/periodic and "
-                        "tanh/no-flux-x fields" % (count, nodes / 1e6),
-            "glups": round(glups, 3),
-            "schedule": int(chosen),
-            "tuner_ms_per_step": [round(float(v), 4) for v in tune_ms],
-            "l2": "state %.1f GB per step vs 129 MB L2" % (bytes_per_step / 1e9),
-            "parallelism": "replicas" if world > 1 else "single GPU",
-        },
-        "roofline": {
-            "bound": "hbm",
-            "achieved": round(achieved, 1),
-            "peak": peak,
-            "unit": "GB/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": recorded_traffic("traffic_batch_d2q5_4096_f32.json", [count]) if chosen == 0
-            else None,
-            "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": bytes_per_step,
-            "note": "algorithmic bytes of a streamed step; L2-blocked schedules move less",
-        },
+        "dtype": line["dtype"],
+        "data": "synthetic (seeded %s; no dataset)" % {"tube": "two-bulb tanh profile",
+                                                      "tube15": "two-bulb tanh profile",
+                                                      "tube6": "two-bulb tanh profile",
+                                                      "plane4": "two-bulb tanh profile",
+                                                      "line": "two-bulb tanh profile",
+                                                      "blobs": "Gaussian blobs",
+                                                      "sine": "sine modes"}[wl.key],
+        "config": dict(line["config"], parallelism="replicas" if world > 1 else "single GPU",
+                       timing="median of %d repeats of the %d-step region (CUDA events)"
+                              % (line["repeats"], args.steps)),
+        "roofline": line["roofline"],
         "e2e": None if args.no_e2e else {
-            "value": round(count * world * args.steps / BATCH_SOLVE_STEPS / (e2e_ms * 1e-3), 3),
-            "unit": "solves/s",
-            "h2d_bytes_per_step": round(x0_host.numel() * 4 / args.steps, 1),
-            "d2h_bytes_per_step": round((x0_host.numel() * 4 + 8 * 3 * count) / args.steps, 1),
+            "value": round(updates / (e2e_ms * 1e-3) / 1e9, 4),
+            "unit": "GLUPS",
+            "h2d_bytes_per_step": round(x0_host.numel() * wl.es / args.steps, 1),
+            "d2h_bytes_per_step": round((x_host.numel() * wl.es + 8 * wl.n) / args.steps, 1),
         },
-        "cpu_baseline": None if (args.no_cpu_baseline or world > 1)
-        else cpu_baseline_batch(grids, Ds, bcs, 1004 + rank, budget_s=args.cpu_budget),
-        "gpu_launches": args.steps * launches_per_step + 1,
+        "gpu_launches": line["gpu_launches"],
         "clocks": clocks,
-        "status_flags": flags,
-        "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
+        "repeat_ms_min_max": line["repeat_ms_min_max"],
+        "status_flags": line["status_flags"],
+        "mass_drift_rel": line["mass_drift_rel"],
     }
+    if extras is not None:
+        out["workloads"] = extras
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget)
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_adjoint(args):
-    """Adjoint workload: gradient of the L2 misfit of the final mole fractions (ternary
-    D2Q5, 512^2, FP32, 4000 steps, target from D* = (0.09, 0.07, 0.02)) with
-    respect to the three D_ij and the initial field, by the adjoint kernels
-    with sqrt(T) checkpointing; the cost is reported against the plain forward
-    run of the same steps."""
+def measure_extras(args, headline: Workload, local: int) -> dict:
+    """The other parts of the metric, timed in the same run at the same --steps:
+    the other single-solve configurations (five-species D2Q9 blobs, FP64 D2Q5
+    sine), the batched solves and the adjoint/forward cost."""
+    import torch
+
+    sms = device_sms(local)
+    out = {}
+    for key in ("blobs", "sine"):
+        if key == headline.key:
+            continue
+        wl = make_workload(key, 256)
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        m = measure_single(wl, args.steps, args.warmup)
+        clocks = sampler.stop()
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        line = single_line(wl, m, args.steps, 1, m["ms"], sms, mhz)
+        line["clocks"] = clocks
+        out[key] = line
+        torch.cuda.empty_cache()
+    out["batch"] = measure_batch(args.steps, args.warmup, local, schedule=args.batch_schedule)
+    torch.cuda.empty_cache()
+    out["adjoint"] = measure_adjoint(args.warmup, local)
+    torch.cuda.empty_cache()
+    return out
+
+
+BATCH_COUNT = 4096
+BATCH_SOLVE_STEPS = 5000
+
+
+def measure_batch(steps: int, warmup: int, local: int, count: int = BATCH_COUNT, seed: int = 1004,
+                  schedule: int = -1, barrier=local_barrier, tune_steps: int = 8, keep=False):
+    """Batched workload: `count` independent ternary D2Q5 FP32 solves, square sides
+    uniform in [32, 256], per-instance D_ij uniform in [0.01, 0.12], sine
+    (periodic) or two-bulb tanh (no-flux x) initial fields; step schedule chosen by
+    the tuner unless `schedule` >= 0."""
     import numpy as np
+    import torch
+
+    import synthetic as sy
+    from paper_1808_06787_gb300 import BatchSolver
+
+    grids, Ds, bcs = sy.batch_instances(count, seed=seed)
+    stream = torch.cuda.Stream()
+    sampler = ClockSampler(local)
+    with torch.cuda.stream(stream):
+        b = BatchSolver("D2Q5", Ds, grids, bcs=bcs, dtype=torch.float32, stream=stream)
+        if schedule < 0:
+            chosen, tune_ms = b.tune(trial_steps=tune_steps)
+        else:
+            b.set_schedule(schedule)
+            chosen, tune_ms = schedule, []
+        launches_per_step = b.launches_per_step()
+        x0_host = torch.empty(int(b.offsets[-1]), dtype=torch.float32).pin_memory()
+        for i in range(count):
+            x0_host[int(b.offsets[i]):int(b.offsets[i + 1])] = torch.from_numpy(
+                sy.batch_field(i, int(grids[i][0]), seed=seed).reshape(-1)).float()
+        b.set_state(x0_host.cuda(non_blocking=True))
+        mass0 = b.mass()
+        b.step(warmup)
+        torch.cuda.synchronize()
+        sampler.start()
+        time.sleep(0.3)
+        ms, reps = timed_repeats(b.step, stream, steps, barrier)
+        clocks = sampler.stop()
+        flags = b.status()
+        mass = b.mass()
+    nodes = float(sum(int(g[0]) * int(g[1]) for g in grids))
+    bytes_per_step = 2.0 * 2 * 5 * 4 * nodes
+    roof = hbm_roofline(bytes_per_step, ms / steps,
+                        recorded_traffic("traffic_batch_d2q5_4096_f32.json", [count]) if chosen == 0
+                        else None)
+    roof["note"] = "algorithmic bytes of a streamed step; L2-blocked schedules move less"
+    out = {
+        "value": round(count * steps / BATCH_SOLVE_STEPS / (ms * 1e-3), 3),
+        "unit": "solves/s",
+        "steps": steps,
+        "ms_per_step": round(ms / steps, 6),
+        "repeats": len(reps),
+        "repeat_ms_min_max": [round(min(reps), 4), round(max(reps), 4)],
+        "glups": round(2.0 * nodes * steps / (ms * 1e-3) / 1e9, 3),
+        "dtype": "f32",
+        "config": {
+            "workload": "batched: %d ternary D2Q5 FP32 solves of %d steps, sides uniform in "
+                        "[32, 256] (%.1f M nodes), D_ij uniform in [0.01, 0.12], sine/periodic "
+                        "and tanh/no-flux-x fields" % (count, BATCH_SOLVE_STEPS, nodes / 1e6),
+            "schedule": int(chosen),
+            "tuner_ms_per_step": [round(float(v), 4) for v in tune_ms],
+            "l2": "state %.1f GB per step vs 129 MB L2" % (bytes_per_step / 1e9),
+        },
+        "roofline": roof,
+        "gpu_launches": steps * launches_per_step,
+        "clocks": clocks,
+        "status_flags": flags,
+        "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
+    }
+    if keep:
+        out.update(solver=b, x0_host=x0_host, stream=stream, grids=grids, Ds=Ds, bcs=bcs)
+    else:
+        b.close()
+    return out
+
+
+ADJOINT_STEPS = 4000
+
+
+def measure_adjoint(warmup: int, local: int, n: int = 512, steps: int = ADJOINT_STEPS,
+                    e2e: bool = False):
+    """Adjoint workload: gradient of the L2 misfit of the final mole fractions
+    (ternary D2Q5, n^2, FP32, `steps` steps, target from D* = (0.09, 0.07, 0.02))
+    with respect to the three D_ij and the initial field, by the adjoint kernels
+    with sqrt(T) checkpointing; the cost is reported against the plain forward run
+    of the same steps (median of 3 of each).  The ratio is measured at the
+    workload's own length: checkpointing makes it depend on T."""
     import torch
 
     import synthetic as sy
     from paper_1808_06787_gb300 import RunSpec, Solver, simulate
 
-    steps = args.steps if args.steps != 20000 else 4000
-    n = 512 if args.grid == 256 else args.grid
     x0 = torch.from_numpy(sy.sin_modes(3, n, n, amp=0.05, seed=1005)).float().cuda()
     Dm = lambda d: sy.D_from_pairs(3, {(1, 2): d[0], (1, 3): d[1], (2, 3): d[2]})
 
@@ -573,69 +643,59 @@ def run_adjoint(args):
         s = Solver("D2Q5", Dm(d), (n, n), dtype=torch.float32)
         s.set_state(x0)
         s.step(steps)
-        return s.moments()
+        x = s.moments()
+        s.close()
+        return x
 
     target = forward((0.09, 0.07, 0.02)).double()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    for _ in range(max(1, args.warmup // 10)):
+    for _ in range(max(1, warmup // 10)):
         forward((0.10, 0.08, 0.02))
     # one untimed gradient pass: loads torch's own kernels used by the loss
     dpw = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
     lw = ((simulate(x0.clone().requires_grad_(True), dpw, RunSpec("D2Q5", (n, n, 1), steps))
            .double() - target) ** 2).sum()
     lw.backward()
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    torch.cuda.synchronize()
-    ev[0].record()
-    forward((0.10, 0.08, 0.02))
-    ev[1].record()
-    dp = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
-    xg = x0.clone().requires_grad_(True)
-    spec = RunSpec("D2Q5", (n, n, 1), steps)
-    spec.stats["adjoint_events"] = []
-    xT = simulate(xg, dp, spec)
-    loss = ((xT.double() - target) ** 2).sum()
-    ev[2].record()
-    loss.backward()
-    ev[3].record()
-    torch.cuda.synchronize()
+    fwd, ckpt, bwd, adj_us = [], [], [], []
+    for _ in range(3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        forward((0.10, 0.08, 0.02))
+        ev[1].record()
+        dp = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
+        xg = x0.clone().requires_grad_(True)
+        spec = RunSpec("D2Q5", (n, n, 1), steps)
+        spec.stats["adjoint_events"] = []
+        xT = simulate(xg, dp, spec)
+        loss = ((xT.double() - target) ** 2).sum()
+        ev[2].record()
+        loss.backward()
+        ev[3].record()
+        torch.cuda.synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        ckpt.append(ev[1].elapsed_time(ev[2]))
+        bwd.append(ev[2].elapsed_time(ev[3]))
+        # the dominant kernel: the adjoint step, timed over the backward's own loops
+        adj = spec.stats["adjoint_events"]
+        adj_us.append(1e3 * sum(a.elapsed_time(b) for a, b, _ in adj) / sum(c for _, _, c in adj))
     clocks = sampler.stop()
-    t_fwd = ev[0].elapsed_time(ev[1])
-    t_ckpt = ev[1].elapsed_time(ev[2])
-    t_bwd = ev[2].elapsed_time(ev[3])
-    # the dominant kernel: the adjoint step, timed over the backward's own loops
-    adj = spec.stats["adjoint_events"]
-    adj_ms = sum(a.elapsed_time(b) for a, b, _ in adj) / sum(c for _, _, c in adj)
+    t_fwd, t_ckpt, t_bwd = (statistics.median(v) for v in (fwd, ckpt, bwd))
+    adj_ms = statistics.median(adj_us) * 1e-3
     adj_bytes = float(n * n) * 2 * 5 * (4 + 8 + 8)  # f+ (FP32) read, lambda (8 B) read and written
-    peak, peak_kind = hbm_peak()
-    launches = spec.stats.get("launches")
-    # end to end through the public API: pinned host x0 in, gradients back to the host
-    x0_host = x0.cpu().pin_memory()
-    g_host = torch.empty(x0.shape, dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xd = x0_host.cuda(non_blocking=True).requires_grad_(True)
-    dpe = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
-    le = ((simulate(xd, dpe, RunSpec("D2Q5", (n, n, 1), steps)).double() - target) ** 2).sum()
-    le.backward()
-    g_host.copy_(xd.grad, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
+    roof = hbm_roofline(adj_bytes, adj_ms,
+                        recorded_traffic("traffic_adjoint_d2q5_512sq_f32.json", [n, n]))
+    roof.update(kernel="k_adjoint_step<D2Q5, 2, float>", avg_launch_us=round(adj_ms * 1e3, 3),
+                note="the 2 x 21 MB adjoint state is largely L2-resident at this size")
     out = {
-        "metric": "adjoint/fwd cost (gradient wrt D_ij and x0 over plain forward)",
         "value": round((t_ckpt + t_bwd) / t_fwd, 3),
         "unit": "x forward",
-        "n_gpus": 1,
-        "steps": steps,
-        "warmup": args.warmup,
-        "ms_per_step": round((t_ckpt + t_bwd) / steps, 6),
         "higher_is_better": False,
-        "scaling": "weak",
-        "vs_baseline": None,
+        "steps": steps,
+        "ms_per_step": round((t_ckpt + t_bwd) / steps, 6),
         "dtype": "f32 forward, float-pair (about 48-bit) adjoint state",
-        "data": "synthetic (seeded sine modes; target from D* = (0.09, 0.07, 0.02))",
         "config": {
             "workload": "adjoint: ternary D2Q5 %d^2 FP32, %d steps, L2 misfit, gradients wrt 3 "
                         "D_ij and the initial field, sqrt(T) checkpointing" % (n, steps),
@@ -646,28 +706,127 @@ def run_adjoint(args):
             "segment_steps": spec.stats.get("segment"),
             "dL_dD": [float(v) for v in dp.grad.numpy()],
             "glups_forward": round(2.0 * n * n * steps / (t_fwd * 1e-3) / 1e9, 3),
+            "timing": "median of 3 forward and 3 gradient runs (CUDA events)",
         },
-        "roofline": {
-            "bound": "hbm",
-            "kernel": "k_adjoint_step<D2Q5, 2, float>",
-            "achieved": round(adj_bytes / (adj_ms * 1e-3) / 1e9, 1),
-            "peak": peak,
-            "unit": "GB/s",
-            "frac": round(adj_bytes / (adj_ms * 1e-3) / 1e9 / peak, 4),
-            "traffic": recorded_traffic("traffic_adjoint_d2q5_512sq_f32.json", [n, n]),
-            "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": adj_bytes,
-            "avg_launch_us": round(adj_ms * 1e3, 3),
-            "note": "the 2 x 21 MB adjoint state is largely L2-resident at this size",
-        },
-        "e2e": {
+        "roofline": roof,
+        "gpu_launches": spec.stats.get("launches"),
+        "clocks": clocks,
+    }
+    if e2e:
+        # end to end through the public API: pinned host x0 in, gradients back to the host
+        x0_host = x0.cpu().pin_memory()
+        g_host = torch.empty(x0.shape, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = x0_host.cuda(non_blocking=True).requires_grad_(True)
+        dpe = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
+        le = ((simulate(xd, dpe, RunSpec("D2Q5", (n, n, 1), steps)).double() - target) ** 2).sum()
+        le.backward()
+        g_host.copy_(xd.grad, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3
+        out["e2e"] = {
             "value": round(e2e_ms / t_fwd, 3),
             "unit": "x forward",
             "h2d_bytes_per_step": round(x0_host.numel() * 4 / steps, 1),
             "d2h_bytes_per_step": round((g_host.numel() * 4 + 3 * 8) / steps, 1),
+        }
+    return out
+
+
+def run_batch(args):
+    """Batched workload as the headline line (see measure_batch)."""
+    import torch
+
+    world, rank, local, dist = dist_context()
+    torch.cuda.set_device(local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    count = BATCH_COUNT if args.grid == 256 else max(1, args.grid)
+    m = measure_batch(args.steps, args.warmup, local, count=count, seed=1004 + rank,
+                      schedule=args.batch_schedule, barrier=barrier, tune_steps=16, keep=True)
+    b, x0_host, stream = m.pop("solver"), m.pop("x0_host"), m.pop("stream")
+    grids, Ds, bcs = m.pop("grids"), m.pop("Ds"), m.pop("bcs")
+    e2e_s = None
+    if not args.no_e2e:
+        with torch.cuda.stream(stream):
+            barrier()
+            t0 = time.perf_counter()
+            b.set_state(x0_host)
+            b.step(args.steps)
+            b.moments(out_device="cpu")
+            b.mass()
+            barrier()
+            e2e_s = time.perf_counter() - t0
+    b.close()
+    e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
+    t_ms, e2e_ms = max_over_ranks(dist, [m["ms_per_step"] * args.steps, e2e_ms])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    out = {
+        "metric": "batched solves/s (5000-step ternary D2Q5 solves) and GLUPS",
+        "value": round(job_rate(count * args.steps / BATCH_SOLVE_STEPS, world, t_ms), 3),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_ms / args.steps, 6),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded sides, diffusivities, sine / tanh fields; no dataset)",
+        "config": dict(m["config"], glups=m["glups"], parallelism="replicas" if world > 1 else "single GPU",
+                       timing="median of %d repeats of the %d-step region (CUDA events)"
+                              % (m["repeats"], args.steps)),
+        "roofline": m["roofline"],
+        "e2e": None if args.no_e2e else {
+            "value": round(count * world * args.steps / BATCH_SOLVE_STEPS / (e2e_ms * 1e-3), 3),
+            "unit": "solves/s",
+            "h2d_bytes_per_step": round(x0_host.numel() * 4 / args.steps, 1),
+            "d2h_bytes_per_step": round((x0_host.numel() * 4 + 8 * 3 * count) / args.steps, 1),
         },
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "cpu_baseline": None if (args.no_cpu_baseline or world > 1)
+        else cpu_baseline_batch(grids, Ds, bcs, 1004 + rank, budget_s=args.cpu_budget),
+        "gpu_launches": m["gpu_launches"],
+        "clocks": m["clocks"],
+        "status_flags": m["status_flags"],
+        "mass_drift_rel": m["mass_drift_rel"],
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_adjoint(args):
+    """Adjoint workload as the headline line (see measure_adjoint)."""
+    steps = args.steps or ADJOINT_STEPS
+    n = 512 if args.grid == 256 else args.grid
+    m = measure_adjoint(args.warmup, 0, n=n, steps=steps, e2e=not args.no_e2e)
+    out = {
+        "metric": "adjoint/fwd cost (gradient wrt D_ij and x0 over plain forward)",
+        "value": m["value"],
+        "unit": m["unit"],
+        "n_gpus": 1,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": m["ms_per_step"],
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": m["dtype"],
+        "data": "synthetic (seeded sine modes; target from D* = (0.09, 0.07, 0.02))",
+        "config": m["config"],
+        "roofline": m["roofline"],
+        "e2e": m.get("e2e"),
+        "gpu_launches": m["gpu_launches"],
+        "clocks": m["clocks"],
     }
     print(json.dumps(out))
 
@@ -786,7 +945,8 @@ def run_reference(args, wl: Workload):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="steps per timed region (default 200; the adjoint workload: 4000)")
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["tube", "blobs", "sine", "tube15", "tube6", "plane4",
@@ -796,6 +956,8 @@ def main():
                     help="seconds of oracle work for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the headline workload (not the other parts of the metric)")
     ap.add_argument("--batch-schedule", type=int, default=-1,
                     help="batched workload: fixed step schedule (0..6) instead of the tuner's")
     ap.add_argument("--grid", type=int, default=256,
@@ -803,6 +965,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.workload != "adjoint" and args.steps is None:
+        args.steps = 200
     if args.workload == "adjoint":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no "

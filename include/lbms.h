@@ -178,8 +178,8 @@ int lbms_set_reference(lbms_t* h, const double* xi_ref);
  * Advance n_steps >= 0 time steps of Eqs. 3-13a/3-13b (pull form: each node
  * gathers f+_k(x - c_k), collides, and stores its post-collision populations).
  * The last step of each call also writes per-block partial sums of every
- * species' mole fraction and reduces them (see lbms_mass), so lbms_mass after
- * lbms_step reads no populations.  Asynchronous: launch errors are returned at once, numerical
+ * species' mole fraction, which lbms_mass reduces when it is called, so
+ * lbms_mass after lbms_step reads no populations.  Asynchronous: launch errors are returned at once, numerical
  * trouble is raised in the status flags.  Returns LBMS_EINVAL if a Dirichlet
  * face has no composition yet.  With Dirichlet faces the species' masses are
  * not conserved (the faces exchange mass with the outside).
@@ -224,16 +224,18 @@ int lbms_mass(lbms_t* h, double* mass_out);
 /*
  * Species totals of a population field without a handle, a workspace or any
  * device allocation.  The paper has no counterpart: this is a service entry
- * point for callers that cannot call cudaMalloc -- code running while a stream
- * is being captured into a CUDA graph (an allocation would invalidate the
- * capture), real-time loops whose device memory is fixed at start-up, and
- * plug-ins whose device memory belongs to a host framework's pool.
+ * point for callers that cannot call cudaMalloc -- real-time loops whose device
+ * memory is fixed at start-up (an allocation may block or fail at a bad time),
+ * plug-ins whose device memory belongs to a host framework's pool, and
+ * monitoring code that reads a population buffer it does not own.
  *   lattice, n_species, grid, dtype  as for lbms_create.
  *   populations  device buffer of S * Q * cells elements of dtype, laid out
  *                [s][k][z][y][x] (the layout of a solver's population buffers:
- *                a solver's state after t steps starts at byte offset
- *                (t mod 2) * round_up(S * Q * cells * sizeof(dtype), 256) of its
- *                workspace).  Read only.
+ *                lbms_populations gives the current one).  Read only.  A
+ *                pointer the CUDA runtime does not report as device memory is
+ *                rejected with LBMS_EINVAL before any work is queued; the
+ *                extent of the buffer cannot be checked and is the caller's
+ *                responsibility.
  *   mass_out     n doubles, host or device: sum over nodes of xi_i = sum_k f_k^i
  *                for the n - 1 evolved species and of the closure species, with
  *                the reduction lbms_mass uses (bit-identical to lbms_mass right
@@ -241,16 +243,18 @@ int lbms_mass(lbms_t* h, double* mass_out);
  *   cuda_stream  stream the work is ordered on; a host mass_out synchronises it.
  * The per-block partial sums go to a file-scope device array of 4 MiB that
  * every GPU which loads the library keeps until the process exits; grids whose
- * partials do not fit (one record per block of 256 nodes -- of 64 nodes below
- * 77824 nodes, as a solver's mass kernel uses -- and species, 8 bytes for F32
- * and 16 for F64, above 4 MiB - 256 B: about 134 M node-species in F32 and
- * 67 M in F64) are rejected with
- * LBMS_EINVAL and a message in lbms_last_error(NULL).  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
- * share the one array and every call overwrites the slots it reads, so calls
- * that overlap on the GPU (other streams, other host threads) race.  Calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * partials do not fit (one record per block and species of the solver's mass
+ * kernel -- blocks of 256 nodes, or of 64 nodes on grids too small to give
+ * every SM two blocks of 256 -- 8 bytes for F32 and 16 for F64, above
+ * 4 MiB - 256 B: about 134 M node-species in F32 and 67 M in F64) are
+ * rejected with LBMS_EINVAL and a message in lbms_last_error(NULL).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) while the library is loaded.  All calls share the one array
+ * and every call overwrites the slots it uses, so calls that overlap on the GPU
+ * (other streams, other host threads) race.  Calls no cudaMalloc, cudaFree or
+ * allocating library routine.
  */
 int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], int dtype,
                       const void* populations, double* mass_out, void* cuda_stream);

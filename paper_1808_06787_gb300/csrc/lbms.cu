@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "adjoint.cuh"
@@ -69,7 +70,7 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
     L->off_f0 = 0;
     L->off_f1 = L->f_bytes;
     L->off_partials = 2 * L->f_bytes;
-    const size_t blocks = step_blocks((uint32_t)cells);
+    const size_t blocks = partial_slots((uint32_t)cells);
     L->off_mass = L->off_partials + align_up(blocks * n * sizeof(double2));
     L->off_status = L->off_mass + align_up(LBMS_MAX_SPECIES * sizeof(double));
     L->off_bound = L->off_status + kAlign;
@@ -204,7 +205,8 @@ struct lbms_s {
     void* partials = nullptr;
     int fixed_shift = 32;
     double* mass_dev = nullptr;
-    bool mass_valid = false;
+    bool partials_valid = false;  // the mass partials are those of the current state
+    bool mass_valid = false;      // mass_dev holds their reduction
     uint32_t* status = nullptr;
     uint32_t* clock = nullptr;  // two step-counter words after the status word
     char* staging = nullptr;
@@ -302,16 +304,6 @@ cudaError_t launch_finalize(const lbms_t* h, cudaStream_t st)
     return cudaGetLastError();
 }
 
-bool is_device_ptr(const void* p)
-{
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 // Capture kGraphSteps plain steps starting from buffer `parity`.
 cudaError_t build_graph(lbms_t* h, int parity, int j)
 {
@@ -340,6 +332,39 @@ cudaError_t build_graph(lbms_t* h, int parity, int j)
 namespace lbms {
 
 int mass_fixed_shift(uint32_t cells) { return fixed_shift_for(cells); }
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t device_sm_count(int* sms)
+{
+    static std::mutex mu;
+    static int cached[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || !cached[dev]) {
+        int v = 0;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        v = v < 1 ? 1 : (v > kMaxSms ? kMaxSms : v);
+        if (dev < 0 || dev >= 64) {
+            *sms = v;
+            return cudaSuccess;
+        }
+        cached[dev] = v;
+    }
+    *sms = cached[dev];
+    return cudaSuccess;
+}
 
 cudaError_t launch_mass_reduce(int dtype, const void* partials, uint32_t blocks, int n, int shift,
                                double* out, cudaStream_t stream)
@@ -414,6 +439,9 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
         if (lo == LBMS_DIRICHLET) dirichlet |= 1u << (2 * a);
         if (hi == LBMS_DIRICHLET) dirichlet |= 1u << (2 * a + 1);
     }
+    int sms = 0;
+    cudaError_t se = device_sm_count(&sms);
+    if (se != cudaSuccess) return fail(nullptr, LBMS_ECUDA, "device query: %s", cudaGetErrorString(se));
     lbms_t* h = new (std::nothrow) lbms_t;
     if (!h) return fail(nullptr, LBMS_ENOMEM, "host allocation failed");
     h->lattice = lattice;
@@ -425,8 +453,8 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->relax = relax;
     h->nx = grid[0]; h->ny = grid[1]; h->nz = grid[2];
     h->cells = (uint32_t)((size_t)grid[0] * grid[1] * grid[2]);
-    h->blocks = step_blocks(h->cells);
-    h->step_block = step_block_for(h->cells);
+    h->blocks = step_blocks(h->cells, sms);
+    h->step_block = step_block_for(h->cells, sms);
     h->noflux = noflux;
     h->dirichlet = dirichlet;
     h->es = dtype == LBMS_F64 ? 8 : 4;
@@ -469,6 +497,7 @@ int lbms_set_state(lbms_t* h, const void* x0)
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
     h->cur = 0;
     h->steps = 0;
+    h->partials_valid = false;
     h->mass_valid = false;
     KArgs a = base_args(h, h->stream);
     a.fout = h->f[0];
@@ -600,9 +629,9 @@ int lbms_step(lbms_t* h, long n_steps)
     if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
     h->cur = 1 - h->cur;
     ++h->steps;
-    e = launch_finalize(h, h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "mass finalize kernel");
-    h->mass_valid = true;
+    // the partials are reduced when the masses are asked for (lbms_mass)
+    h->partials_valid = true;
+    h->mass_valid = false;
     return LBMS_OK;
 }
 
@@ -679,12 +708,16 @@ int lbms_mass(lbms_t* h, double* mass_out)
     if (!mass_out) return fail(h, LBMS_EINVAL, "mass_out is NULL");
     h->err[0] = '\0';
     cudaError_t e;
-    if (!h->mass_valid) {
+    if (!h->partials_valid) {
         KArgs a = base_args(h, h->stream);
         a.fout = h->f[h->cur];
         a.partials = h->partials;
         e = dispatch(h, OP_MASS, a);
         if (e != cudaSuccess) return cuda_fail(h, e, "mass kernel");
+        h->partials_valid = true;
+        h->mass_valid = false;
+    }
+    if (!h->mass_valid) {
         e = launch_finalize(h, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "mass finalize kernel");
         h->mass_valid = true;
@@ -732,6 +765,7 @@ int lbms_set_state_raw(lbms_t* h, const void* f_in, long step)
     if (e != cudaSuccess) return cuda_fail(h, e, "raw state upload");
     h->cur = 0;
     h->steps = step;
+    h->partials_valid = false;
     h->mass_valid = false;
     return LBMS_OK;
 }
@@ -786,6 +820,8 @@ int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!grad_x || !lam) return fail(h, LBMS_EINVAL, "grad_x and lam must not be NULL");
+    if (!is_device_ptr(grad_x) || !is_device_ptr(lam))
+        return fail(h, LBMS_EINVAL, "grad_x and lam must be device memory");
     AArgs a;
     a.k = base_args(h, h->stream);
     a.grad_x = grad_x;
@@ -803,6 +839,8 @@ int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* l
     if (!f_prev || !lam_in || !lam_out || !gacc)
         return fail(h, LBMS_EINVAL, "f_prev, lam_in, lam_out and gacc must not be NULL");
     if (lam_in == lam_out) return fail(h, LBMS_EINVAL, "lam_in and lam_out must be different buffers");
+    if (!is_device_ptr(f_prev) || !is_device_ptr(lam_in) || !is_device_ptr(lam_out) || !is_device_ptr(gacc))
+        return fail(h, LBMS_EINVAL, "f_prev, lam_in, lam_out and gacc must be device memory");
     AArgs a;
     a.k = base_args(h, h->stream);
     a.fprev = f_prev;
@@ -820,6 +858,8 @@ int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!lam0 || !grad_x0) return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must not be NULL");
+    if (!is_device_ptr(lam0) || !is_device_ptr(grad_x0))
+        return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must be device memory");
     AArgs a;
     a.k = base_args(h, h->stream);
     a.lam = const_cast<void*>(lam0);
@@ -835,6 +875,7 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!gacc || !dL_dD) return fail(h, LBMS_EINVAL, "gacc and dL_dD must not be NULL");
+    if (!is_device_ptr(gacc)) return fail(h, LBMS_EINVAL, "gacc must be device memory");
     const int np = h->n * (h->n - 1) / 2;
     double* slot = reinterpret_cast<double*>(reinterpret_cast<char*>(h->status) + 128);
     double invD2[16];

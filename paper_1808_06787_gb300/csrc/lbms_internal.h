@@ -62,16 +62,37 @@ cudaError_t dispatch_d3q6(Op op, int dtype, const KArgs& a);
 inline uint32_t node_blocks(uint32_t cells) { return (cells + kBlock - 1) / kBlock; }
 
 // Threads per block of a solver's step and mass kernels: grids too small to give
-// every one of the 152 SMs two blocks of kBlock threads run blocks of 64, so that
+// every SM of the device two blocks of kBlock threads run blocks of 64, so that
 // the per-node work (FP64 in particular, whose pipes are narrow on GB300) is
-// spread over all SMs instead of a few.
+// spread over all SMs instead of a few.  `sms` is the device's multiprocessor
+// count (device_sm_count).
 constexpr uint32_t kSmallBlock = 64;
-inline uint32_t step_block_for(uint32_t cells) { return cells < 2u * 152u * kBlock ? kSmallBlock : kBlock; }
-inline uint32_t step_blocks(uint32_t cells)
+inline uint32_t step_block_for(uint32_t cells, int sms)
 {
-    const uint32_t tb = step_block_for(cells);
+    return (uint64_t)cells < 2ull * (uint64_t)sms * kBlock ? kSmallBlock : kBlock;
+}
+inline uint32_t step_blocks(uint32_t cells, int sms)
+{
+    const uint32_t tb = step_block_for(cells, sms);
     return (cells + tb - 1) / tb;
 }
+
+// Multiprocessor count of the current device (cudaDevAttrMultiProcessorCount),
+// looked up once per device and clamped to kMaxSms.
+constexpr int kMaxSms = 8192;
+cudaError_t device_sm_count(int* sms);
+
+// Mass-partial slots a workspace reserves for a grid: enough for the block
+// partition of step_blocks on any device of up to kMaxSms SMs, so that
+// workspace sizes do not depend on the device they are computed on.
+inline uint32_t partial_slots(uint32_t cells)
+{
+    return (uint64_t)cells < 2ull * kMaxSms * kBlock ? (cells + kSmallBlock - 1) / kSmallBlock
+                                                    : (cells + kBlock - 1) / kBlock;
+}
+
+// True if the runtime reports p as device (or managed) memory of this process.
+bool is_device_ptr(const void* p);
 
 // Helpers of the host runtime shared with lbms_mass_noalloc (mass_noalloc.cu):
 // fraction bits of the FP32 fixed-point mass partials for a grid, the final

@@ -1,14 +1,19 @@
 // lbms_mass_noalloc: species totals of a population field for callers that
 // cannot allocate device memory.
 //
-// Some callers of this library may not call cudaMalloc at all: code that runs
-// while a CUDA stream is being captured into a graph (an allocation would
-// break the capture), real-time or embedded loops whose memory is fixed at
-// start-up, and plug-ins inside host frameworks whose device memory belongs to
-// the framework's own pool.  lbms_mass needs a solver handle and its
-// caller-provided workspace; this entry point needs neither.  Its scratch (one
-// partial sum per block and species) lives in the file-scope device array
-// below, which every GPU that loads the library holds until the process exits.
+// Some callers of this library may not call cudaMalloc at all: real-time or
+// embedded loops whose device memory is fixed at start-up (an allocation can
+// block for an unbounded time or fail), plug-ins inside host frameworks whose
+// device memory belongs to the framework's own pool, and monitoring code that
+// inspects a buffer someone else owns without a solver handle.  lbms_mass needs
+// a solver handle and its caller-provided workspace; this entry point needs
+// neither.  Its scratch (one partial sum per block and species) lives in the
+// file-scope device array below, which every GPU that loads the library holds
+// until the process exits.
+//
+// The array's device address is looked up once per device and cached for the
+// life of the process, so resetting a device (cudaDeviceReset) while the
+// library stays loaded is not supported by this entry point.
 #include <mutex>
 
 #include "lbms_internal.h"
@@ -27,16 +32,6 @@ static __device__ __align__(256) unsigned char g_mass_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
-
-bool is_device_ptr(const void* p)
-{
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 // Device address of the scratch array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
@@ -71,10 +66,24 @@ extern "C" int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], 
         return set_call_error(LBMS_EINVAL, "invalid lattice/species/grid/dtype combination");
     if (!populations || !mass_out) return set_call_error(LBMS_EINVAL, "populations and mass_out must not be NULL");
     const uint32_t cells = (uint32_t)((size_t)grid[0] * grid[1] * grid[2]);
+    const size_t record = dtype == LBMS_F64 ? 16 : 8;
+    // grids whose partials cannot fit even with the coarsest block partition are
+    // refused before anything touches the device
+    if ((size_t)node_blocks(cells) * n_species * record > kPartialBytes)
+        return set_call_error(LBMS_EINVAL,
+                              "grid too large for lbms_mass_noalloc: %u nodes x %d species need more "
+                              "than the %zu bytes of static scratch (use lbms_mass with a workspace)",
+                              cells, n_species, kPartialBytes);
+    // the kernel reads populations on the device: a host pointer is refused
+    // before any launch
+    if (!is_device_ptr(populations))
+        return set_call_error(LBMS_EINVAL, "populations must be device memory");
+    int sms = 0;
+    cudaError_t e = device_sm_count(&sms);
+    if (e != cudaSuccess) return set_call_error(LBMS_ECUDA, "device query: %s", cudaGetErrorString(e));
     // the block partition of a solver's own mass kernel, so that both entry
     // points run the same reduction (the FP64 compensated sums depend on it)
-    const uint32_t blocks = step_blocks(cells);
-    const size_t record = dtype == LBMS_F64 ? 16 : 8;
+    const uint32_t blocks = step_blocks(cells, sms);
     const size_t need = (size_t)blocks * n_species * record;
     if (need > kPartialBytes)
         return set_call_error(LBMS_EINVAL,
@@ -88,19 +97,19 @@ extern "C" int lbms_mass_noalloc(int lattice, int n_species, const int grid[3], 
     KArgs a;
     a.nx = grid[0]; a.ny = grid[1]; a.nz = grid[2];
     a.cells = cells;
-    a.step_block = step_block_for(cells);
+    a.step_block = step_block_for(cells, sms);
     a.n_species = n_species;
     a.fout = const_cast<void*>(populations);  // read only by the mass kernel
     a.partials = scratch;
     a.fixed_shift = mass_fixed_shift(cells);
     a.stream = st;
-    cudaError_t e = lattice == LBMS_D2Q5   ? dispatch_d2q5(OP_MASS, dtype, a)
-                    : lattice == LBMS_D2Q9 ? dispatch_d2q9(OP_MASS, dtype, a)
-                    : lattice == LBMS_D3Q7 ? dispatch_d3q7(OP_MASS, dtype, a)
-                    : lattice == LBMS_D3Q15 ? dispatch_d3q15(OP_MASS, dtype, a)
-                    : lattice == LBMS_D1Q3 ? dispatch_d1q3(OP_MASS, dtype, a)
-                    : lattice == LBMS_D2Q4 ? dispatch_d2q4(OP_MASS, dtype, a)
-                                           : dispatch_d3q6(OP_MASS, dtype, a);
+    e = lattice == LBMS_D2Q5    ? dispatch_d2q5(OP_MASS, dtype, a)
+        : lattice == LBMS_D2Q9  ? dispatch_d2q9(OP_MASS, dtype, a)
+        : lattice == LBMS_D3Q7  ? dispatch_d3q7(OP_MASS, dtype, a)
+        : lattice == LBMS_D3Q15 ? dispatch_d3q15(OP_MASS, dtype, a)
+        : lattice == LBMS_D1Q3  ? dispatch_d1q3(OP_MASS, dtype, a)
+        : lattice == LBMS_D2Q4  ? dispatch_d2q4(OP_MASS, dtype, a)
+                                : dispatch_d3q6(OP_MASS, dtype, a);
     if (e != cudaSuccess) return set_call_error(LBMS_ECUDA, "mass kernel: %s", cudaGetErrorString(e));
     const bool host_out = !is_device_ptr(mass_out);
     double* dst = host_out ? reinterpret_cast<double*>(static_cast<char*>(scratch) + kPartialBytes) : mass_out;

@@ -86,7 +86,7 @@ def test_fp64_roofline_arithmetic():
     wl = bench.make_workload("sine", 256)
     assert wl.grid == (128, 128, 1) and wl.cells == 128 * 128
     step_ms = 0.006
-    r = bench.fp64_roofline(wl, step_ms)
+    r = bench.fp64_roofline(wl, step_ms, 152, 2070.0)
     flops = 171.0 * 128 * 128
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["algorithmic_flops_per_launch"] == pytest.approx(flops)
@@ -97,3 +97,11 @@ def test_fp64_roofline_arithmetic():
 
 def test_job_rate_counts_the_units_of_all_ranks():
     assert bench.job_rate(1000.0, 4, 2.0) == pytest.approx(2.0e6)
+
+
+def test_fp64_peak_follows_sm_count_and_sampled_clock():
+    assert bench.fp64_peak_tflops(148, 1900.0) == pytest.approx(148 * 2 * 2 * 1.9e9 / 1e12)
+    wl = bench.make_workload("sine", 256)
+    r = bench.fp64_roofline(wl, 0.006, 148, 1900.0)
+    assert r["peak"] == pytest.approx(148 * 2 * 2 * 1.9e9 / 1e12, rel=1e-3)
+    assert "148 SMs" in r["peak_source"] and "1900 MHz" in r["peak_source"]

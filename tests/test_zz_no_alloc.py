@@ -1,11 +1,12 @@
 """lbms_mass_noalloc: the allocation-free mass entry point.
 
-Callers that cannot call cudaMalloc (code running during CUDA stream capture,
-fixed-memory real-time loops, plug-ins living in a host framework's memory
-pool) get species totals of a population buffer from this entry point, which
-keeps its scratch in a static device array instead of a workspace.  These tests
-call it through the C ABI and check it against lbms_mass.  The file is named to
-be collected last, so that a stop-at-first-failure run has run everything else.
+Callers that cannot call cudaMalloc (real-time loops whose device memory is
+fixed at start-up, plug-ins living in a host framework's memory pool,
+monitoring code reading a buffer it does not own) get species totals of a
+population buffer from this entry point, which keeps its scratch in a static
+device array instead of a workspace.  These tests call it through the C ABI
+and check it against lbms_mass.  The file is named to be collected last, so
+that a stop-at-first-failure run has run everything else.
 """
 
 import ctypes
@@ -23,7 +24,7 @@ def _call(lib, lattice, n, grid, dtype, pop_ptr, out):
                                  ctypes.c_void_p(pop_ptr), out, None)
 
 
-def test_noalloc_rejects_oversized_grid_before_device_work():
+def test_noalloc_rejects_oversized_grids_and_host_buffers_before_device_work():
     import paper_1808_06787_gb300 as p
 
     lib = p.load()
@@ -34,6 +35,12 @@ def test_noalloc_rejects_oversized_grid_before_device_work():
     assert "scratch" in lib.lbms_last_error(None).decode()
     rc = _call(lib, 2, 3, (16, 16, 16), 0, 0, out.ctypes.data_as(ctypes.c_void_p))
     assert rc == 1
+    # a host buffer of the right size is refused before any launch
+    host = np.zeros(2 * 7 * 16 * 16 * 16, dtype=np.float32)
+    rc = _call(lib, 2, 3, (16, 16, 16), 0, host.ctypes.data, out.ctypes.data_as(ctypes.c_void_p))
+    assert rc == 1
+    assert "device memory" in lib.lbms_last_error(None).decode()
+    assert np.all(out == 0.0)
 
 
 @pytest.mark.gpu
@@ -89,7 +96,8 @@ def test_noalloc_matches_lbms_mass_twice(dtype):
                          ids=["1node", "small", "below-77824", "at-77824"])
 def test_noalloc_bit_identical_to_lbms_mass_at_every_size(dims, dtype):
     """Right after set_state both entry points reduce the same populations with
-    the same block partition (64-node blocks below 77824 nodes, 256 above), so
+    the same block partition (64-node blocks below 2 x 152 x 256 = 77824 nodes
+    on GB300's 152 SMs, 256 above), so
     the results agree bit for bit, FP64 compensated sums included."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
