@@ -69,8 +69,9 @@ enum { LBMS_F32 = 0, LBMS_F64 = 1 };
  * of Sec. 4, f_k(x_f, t+1) = -f+_kbar(x_f, t) + 2 w_kbar xi_{i,b} (set with
  * lbms_set_boundary).  A D2Q9 diagonal link leaving through two wall faces at
  * a corner takes the kind (and composition) of the first of them in axis
- * order x, y, z. */
-enum { LBMS_PERIODIC = 0, LBMS_NOFLUX = 1, LBMS_DIRICHLET = 2 };
+ * order x, y, z.  HALO marks a cut of a slab decomposition (see "Slab
+ * decomposition" below): only on the faces of the split axis. */
+enum { LBMS_PERIODIC = 0, LBMS_NOFLUX = 1, LBMS_DIRICHLET = 2, LBMS_HALO = 3 };
 
 /* Relaxation of the even moments.  MAGIC: Lambda_2 by Eq. 3-16 (off-diagonal
  * entries equal Lambda_1, diagonal 8 (l - 2) / (l - 8)).  SRT: Lambda_2 =
@@ -106,8 +107,9 @@ enum {
  * Bytes of device workspace that lbms_create needs for this problem: two
  * population buffers of S * Q * cells elements (ping-pong), per-block partial
  * sums for the mass diagnostic, a status word, the compositions of Dirichlet
- * faces and a staging area (at most 16 MiB) for host input/output.  Returns 0
- * for an invalid combination.
+ * faces, the halo buffers of the two faces of the split axis (slab
+ * decomposition; a few layers of nodes) and a staging area (at most 16 MiB)
+ * for host input/output.  Returns 0 for an invalid combination.
  */
 size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dtype);
 
@@ -126,7 +128,8 @@ size_t lbms_workspace_size(int lattice, int n_species, const int grid[3], int dt
  *              needs lbms_set_reference before the first step; the adjoint
  *              entry points reject it).
  *   bc         host array of 6 face kinds {x-low, x-high, y-low, y-high, z-low,
- *              z-high}, each LBMS_PERIODIC, LBMS_NOFLUX or LBMS_DIRICHLET; a
+ *              z-high}, each LBMS_PERIODIC, LBMS_NOFLUX or LBMS_DIRICHLET, or
+ *              LBMS_HALO on a face of the split axis (slab decomposition); a
  *              periodic face must be paired with a periodic face on the same
  *              axis.  Unused z faces of a 2D lattice are ignored.  Every
  *              Dirichlet face needs lbms_set_boundary before the first step.
@@ -340,6 +343,52 @@ const char* lbms_last_error(const lbms_t* h);
 
 /* Release the handle.  Does not free the caller's workspace. */
 void lbms_destroy(lbms_t* h);
+
+/* ========================================================================= */
+/* Slab decomposition: one grid split into slabs along its split axis -- the  */
+/* lattice's last axis (z for D3Q7, D3Q15, D3Q6; y for D2Q5, D2Q9, D2Q4; x    */
+/* for D1Q3), so that a layer of nodes is contiguous -- each slab a handle of */
+/* its own (on one GPU, or one per GPU), with one exchange per time step.     */
+/* ========================================================================= */
+/*
+ * The propagation of Eq. 3-13b is nearest-neighbour: a step of a slab needs,
+ * beyond its own populations, only the populations of the neighbouring slabs'
+ * boundary layers that cross the cut towards it (1 per species and node for
+ * D2Q5, D3Q7, D2Q4, D3Q6 and D1Q3, 3 for D2Q9, 5 for D3Q15).  A slab is a handle
+ * created with LBMS_HALO on the faces of the split axis that are cuts (the
+ * slab's grid is its own share of the layers; the other axes and their faces
+ * are those of the whole grid; a wrapping split axis makes both ends cuts).
+ * Every step also writes the slab's own crossing populations into a send
+ * buffer per cut face; before each step the caller copies each neighbour's
+ * send buffer into this slab's receive buffer of the same face, and the step
+ * reads it as the populations beyond the cut.  Fields, masses (lbms_mass) and
+ * fluxes of a slab are those of its own nodes.
+ *
+ * lbms_set_subdomain    sets the index, in the undivided grid, of the slab's
+ *                       first layer along the split axis.  FP32 solvers key
+ *                       their stochastic rounding by the node index, so with
+ *                       it the slabs of a decomposed run evolve bit for bit as
+ *                       the undivided grid does.  Call before the first step.
+ * lbms_halo_buffers     device addresses (inside the workspace) of the send
+ *                       buffer of cut face `face` (0..5, as bc) and of the
+ *                       receive buffer the next step reads, and their size in
+ *                       bytes; the layout of both is [populations crossing the
+ *                       face][S][layer nodes].  The receive buffer alternates
+ *                       with the population buffers, so ask again before every
+ *                       exchange.  lbms_set_state fills the send buffers too.
+ * lbms_slab_step        n_steps steps of `count` slabs of one grid on one GPU,
+ *                       given in split-axis order, all on one stream and at the
+ *                       same step: each step copies the send buffers into the
+ *                       neighbours' receive buffers (device-to-device) and then
+ *                       steps every slab.  Errors go to lbms_last_error(subs[0])
+ *                       (or lbms_last_error(NULL) for NULL arguments).
+ * lbms_step on a slab with LBMS_HALO faces takes n_steps <= 1 (the exchange
+ * belongs between steps).  lbms_set_state_raw, lbms_recompute and the adjoint
+ * entry points reject slabs; batched solves do not take LBMS_HALO.
+ */
+int lbms_set_subdomain(lbms_t* h, long first_layer);
+int lbms_halo_buffers(lbms_t* h, int face, void** send, void** recv, size_t* bytes);
+int lbms_slab_step(lbms_t* const* subs, int count, long n_steps);
 
 /* ========================================================================= */
 /* Batched solves: many independent problems of one lattice, species count   */

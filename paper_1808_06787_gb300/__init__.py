@@ -26,4 +26,5 @@ from .lbms import (  # noqa: F401
     load,
 )
 from .autograd import MaxwellStefanLB, RunSpec, simulate  # noqa: F401
+from .slab import DistSlabSolver, SlabSolver  # noqa: F401
 from . import scenarios  # noqa: F401

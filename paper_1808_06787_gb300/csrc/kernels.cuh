@@ -48,6 +48,7 @@ struct StepParams {
     const uint32_t* clock_in;
     uint32_t* clock_out;
     const T* __restrict__ xb;  // Dirichlet face compositions [6][S]
+    Halo<T> halo;              // slab cuts: receive buffers of fin's parity, send buffers
     Coeffs<T> co;
 };
 
@@ -205,18 +206,21 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
     if (active) {
         const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb);
+        pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb, &p.halo);
         mole_fractions<LAT, S, T>(f, xi);
         if (MASS) check_range<S, T>(xi, p.status);  // once per lbms_step call
         T L1[S][S], L2[S][S];
         T xl[S + 1];
         lambda_composition<S, T>(xi, p.co, p.relax, xl);
         relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
-        collide<LAT, S, T>(f, xi, L1, L2, mix32(step * 0x9e3779b9u) ^ (cell * 0x27d4eb2du));
+        // the rounding key uses the node's index in the undivided grid, so that
+        // the slabs of a decomposed grid round as the whole grid does
+        collide<LAT, S, T>(f, xi, L1, L2, mix32(step * 0x9e3779b9u) ^ ((cell + p.g.origin) * 0x27d4eb2du));
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.g.cells + cell] = f[s][k];
+        if (h.hal) pack_halo<LAT, S, T>(f, p.g, h, p.halo);
     }
     if (MASS) write_mass_partials<S>(xi, active, p.mass);
 }
@@ -253,6 +257,7 @@ struct FieldParams {
     int relax;
     uint32_t* status;
     const T* xb;      // Dirichlet face compositions [6][S]
+    Halo<T> halo;     // slab cuts: receive buffers of fprev's parity (moments), send buffers (init)
     Coeffs<T> co;
 };
 
@@ -278,6 +283,7 @@ __global__ void __launch_bounds__(kBlock) k_init(FieldParams<T> p)
     if (!finite || !(fabs(sum - 1.0) <= 1e-5)) atomicOr(p.status, LBMS_FLAG_INIT);
     // moving populations w_k xi; the rest population takes what is left of xi,
     // so that sum_k f_k = xi up to one rounding whatever the weights round to
+    T f[S][Q];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         T moving = T(0);
@@ -285,9 +291,15 @@ __global__ void __launch_bounds__(kBlock) k_init(FieldParams<T> p)
         for (int k = 1; k < Q; ++k) {
             const T fk = T(L::w(k)) * xi[s];
             moving += fk;
+            f[s][k] = fk;
             p.fcur[(size_t)(s * Q + k) * p.g.cells + cell] = fk;
         }
-        p.fcur[(size_t)(s * Q) * p.g.cells + cell] = xi[s] - moving;
+        f[s][0] = xi[s] - moving;
+        p.fcur[(size_t)(s * Q) * p.g.cells + cell] = f[s][0];
+    }
+    if (p.g.halo) {  // a slab: its cut layers also fill the send buffers
+        const Neighbourhood h = neighbourhood<L::DIM>(p.g, cell);
+        if (h.hal) pack_halo<LAT, S, T>(f, p.g, h, p.halo);
     }
 }
 
@@ -324,7 +336,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
     if (p.fprev) {
         const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
+        pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb, &p.halo);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         T L1[S][S], L2[S][S];
@@ -356,6 +368,17 @@ Coeffs<T> make_coeffs(const KArgs& a)
     return c;
 }
 
+template <typename T>
+Halo<T> make_halo(const KArgs& a)
+{
+    Halo<T> h;
+    h.recv_lo = static_cast<const T*>(a.halo_recv[0]);
+    h.recv_hi = static_cast<const T*>(a.halo_recv[1]);
+    h.send_lo = static_cast<T*>(a.halo_send[0]);
+    h.send_hi = static_cast<T*>(a.halo_send[1]);
+    return h;
+}
+
 inline FastDiv make_fastdiv(uint32_t d)
 {
     uint32_t l = 0;
@@ -374,6 +397,9 @@ inline Geom make_geom(const KArgs& a)
     g.cells = a.cells;
     g.noflux = a.noflux | a.dirichlet;
     g.dirichlet = a.dirichlet;
+    g.halo = a.halo;
+    g.plane = a.plane;
+    g.origin = a.origin;
     g.dnx = make_fastdiv((uint32_t)a.nx);
     g.dny = make_fastdiv((uint32_t)a.ny);
     return g;
@@ -394,6 +420,7 @@ cudaError_t launch(Op op, const KArgs& a)
         p.clock_in = a.clock_in;
         p.clock_out = a.clock_out;
         p.xb = static_cast<const T*>(a.xb);
+        p.halo = make_halo<T>(a);
         p.co = make_coeffs<T>(a);
         const uint32_t tb = a.step_block;
         const uint32_t blocks = (a.cells + tb - 1) / tb;
@@ -414,6 +441,7 @@ cudaError_t launch(Op op, const KArgs& a)
     p.relax = a.relax;
     p.status = a.status;
     p.xb = static_cast<const T*>(a.xb);
+    p.halo = make_halo<T>(a);
     p.co = make_coeffs<T>(a);
     const uint32_t blocks = node_blocks(a.c1 - a.c0);
     if (blocks == 0) return cudaSuccess;

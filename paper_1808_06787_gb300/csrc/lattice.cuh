@@ -131,6 +131,36 @@ struct Lattice<LBMS_D3Q6> {
     __host__ __device__ static constexpr double cs2() { return 1.0 / 3.0; }
 };
 
+// Slab decomposition: a grid is split along its slowest axis (z for the 3D
+// lattices, y for the 2D ones, x for D1Q3), so that one layer of nodes is a
+// contiguous run of `plane` node indices.  split_c(k) is the velocity component
+// of direction k along that axis; the populations with split_c(k) = +1 (resp.
+// -1) are the ones that cross a cut upward (downward), and halo_slot(k) is the
+// index of k among them in the device order.
+template <int LAT>
+__host__ __device__ constexpr int split_c(int k)
+{
+    using L = Lattice<LAT>;
+    return L::DIM == 3 ? L::cz(k) : (L::DIM == 2 ? L::cy(k) : L::cx(k));
+}
+
+template <int LAT>
+__host__ __device__ constexpr int halo_slot(int k)
+{
+    int j = 0;
+    for (int i = 0; i < k; ++i) j += split_c<LAT>(i) == split_c<LAT>(k) ? 1 : 0;
+    return j;
+}
+
+// Number of populations that cross a cut in one direction.
+template <int LAT>
+__host__ __device__ constexpr int halo_width()
+{
+    int n = 0;
+    for (int k = 0; k < Lattice<LAT>::Q; ++k) n += split_c<LAT>(k) > 0 ? 1 : 0;
+    return n;
+}
+
 // The opposite direction of k in the device order.
 template <int LAT>
 __host__ __device__ constexpr int opp(int k)

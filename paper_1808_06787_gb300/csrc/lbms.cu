@@ -49,9 +49,31 @@ int lattice_dim(int lat)
 bool adjoint_lattice(int lat) { return lat != LBMS_D2Q4 && lat != LBMS_D3Q6; }
 
 struct Layout {
-    size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_bound, off_staging,
-        staging_bytes, total;
+    size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_bound, off_halo,
+        halo_bytes, off_staging, staging_bytes, total;
 };
+
+// Populations crossing a cut of the split axis in one direction.
+int lattice_halo_width(int lat)
+{
+    switch (lat) {
+        case LBMS_D2Q5: return halo_width<LBMS_D2Q5>();
+        case LBMS_D2Q9: return halo_width<LBMS_D2Q9>();
+        case LBMS_D3Q7: return halo_width<LBMS_D3Q7>();
+        case LBMS_D3Q15: return halo_width<LBMS_D3Q15>();
+        case LBMS_D1Q3: return halo_width<LBMS_D1Q3>();
+        case LBMS_D2Q4: return halo_width<LBMS_D2Q4>();
+        case LBMS_D3Q6: return halo_width<LBMS_D3Q6>();
+        default: return 0;
+    }
+}
+
+// Nodes per layer of the split axis (the slowest axis of the lattice's dimension).
+size_t split_plane(int lat, const int grid[3])
+{
+    const int dim = lattice_dim(lat);
+    return dim == 3 ? (size_t)grid[0] * grid[1] : (dim == 2 ? (size_t)grid[0] : 1);
+}
 
 bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
 {
@@ -74,7 +96,11 @@ bool make_layout(int lat, int n, const int grid[3], int dtype, Layout* L)
     L->off_mass = L->off_partials + align_up(blocks * n * sizeof(double2));
     L->off_status = L->off_mass + align_up(LBMS_MAX_SPECIES * sizeof(double));
     L->off_bound = L->off_status + kAlign;
-    L->off_staging = L->off_bound + align_up(6 * LBMS_MAX_SPECIES * sizeof(double));
+    L->off_halo = L->off_bound + align_up(6 * LBMS_MAX_SPECIES * sizeof(double));
+    // slab cuts: per face of the split axis a send buffer and one receive buffer
+    // per population-buffer parity, [halo_width][S][plane] each
+    L->halo_bytes = align_up((size_t)lattice_halo_width(lat) * (n - 1) * split_plane(lat, grid) * es);
+    L->off_staging = L->off_halo + 6 * L->halo_bytes;
     size_t want = (size_t)n * (1 + dim) * cells * es;
     L->staging_bytes = align_up(want < kStagingMax ? want : kStagingMax);
     L->total = L->off_staging + L->staging_bytes;
@@ -192,6 +218,11 @@ struct lbms_s {
     uint32_t step_block = 256;        // their threads per block
     uint32_t noflux = 0;
     uint32_t dirichlet = 0;  // Dirichlet faces
+    uint32_t halo = 0;       // slab cut faces (LBMS_HALO)
+    uint32_t plane = 1;      // nodes per layer of the split axis
+    uint32_t origin = 0;     // global index of node 0 (lbms_set_subdomain)
+    void* halo_send[2] = {nullptr, nullptr};                // [face: low, high]
+    void* halo_recv[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [parity][face]
     uint32_t xb_set = 0;     // Dirichlet faces whose composition has been set
     void* xb = nullptr;      // device [6][S] compositions of the Dirichlet faces, solver dtype
     size_t es = 4;
@@ -271,6 +302,11 @@ KArgs base_args(const lbms_t* h, cudaStream_t st)
     a.noflux = h->noflux;
     a.dirichlet = h->dirichlet;
     a.xb = h->xb;
+    a.halo = h->halo;
+    a.plane = h->plane;
+    a.origin = h->origin;
+    a.halo_send[0] = h->halo_send[0];
+    a.halo_send[1] = h->halo_send[1];
     a.relax = h->relax;
     a.n_species = h->n;
     memcpy(a.invD, h->invD, sizeof(a.invD));
@@ -287,6 +323,8 @@ cudaError_t launch_step(const lbms_t* h, int src, bool mass, cudaStream_t st)
     KArgs a = base_args(h, st);
     a.fin = h->f[src];
     a.fout = h->f[1 - src];
+    a.halo_recv[0] = h->halo_recv[src][0];
+    a.halo_recv[1] = h->halo_recv[src][1];
     a.partials = h->partials;
     a.clock_in = h->clock + src;
     a.clock_out = h->clock + (1 - src);
@@ -427,17 +465,22 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
                 return fail(nullptr, LBMS_EINVAL, "D is not symmetric at (%d, %d)", i, j);
         }
     const int dim = lattice_dim(lattice);
-    uint32_t noflux = 0, dirichlet = 0;
+    uint32_t noflux = 0, dirichlet = 0, halo = 0;
     for (int a = 0; a < dim; ++a) {
         const int lo = bc[2 * a], hi = bc[2 * a + 1];
-        if (lo < LBMS_PERIODIC || lo > LBMS_DIRICHLET || hi < LBMS_PERIODIC || hi > LBMS_DIRICHLET)
+        if (lo < LBMS_PERIODIC || lo > LBMS_HALO || hi < LBMS_PERIODIC || hi > LBMS_HALO)
             return fail(nullptr, LBMS_EINVAL, "invalid face kind on axis %d", a);
+        if ((lo == LBMS_HALO || hi == LBMS_HALO) && a != dim - 1)
+            return fail(nullptr, LBMS_EINVAL,
+                        "LBMS_HALO faces belong to the split axis (the lattice's last axis), not axis %d", a);
         if ((lo == LBMS_PERIODIC) != (hi == LBMS_PERIODIC))
             return fail(nullptr, LBMS_EINVAL, "a periodic face must be paired on axis %d", a);
         if (lo == LBMS_NOFLUX) noflux |= 1u << (2 * a);
         if (hi == LBMS_NOFLUX) noflux |= 1u << (2 * a + 1);
         if (lo == LBMS_DIRICHLET) dirichlet |= 1u << (2 * a);
         if (hi == LBMS_DIRICHLET) dirichlet |= 1u << (2 * a + 1);
+        if (lo == LBMS_HALO) halo |= 1u << (2 * a);
+        if (hi == LBMS_HALO) halo |= 1u << (2 * a + 1);
     }
     int sms = 0;
     cudaError_t se = device_sm_count(&sms);
@@ -457,6 +500,8 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->step_block = step_block_for(h->cells, sms);
     h->noflux = noflux;
     h->dirichlet = dirichlet;
+    h->halo = halo;
+    h->plane = (uint32_t)split_plane(lattice, grid);
     h->es = dtype == LBMS_F64 ? 8 : 4;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) h->invD[i][j] = i == j ? 0.0 : 1.0 / D[i * n + j];
@@ -471,6 +516,11 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
     h->clock = h->status + 16;
     h->staging = h->ws + L.off_staging;
     h->xb = h->ws + L.off_bound;
+    for (int f = 0; f < 2; ++f) {
+        h->halo_send[f] = h->ws + L.off_halo + (size_t)(3 * f) * L.halo_bytes;
+        h->halo_recv[0][f] = h->ws + L.off_halo + (size_t)(3 * f + 1) * L.halo_bytes;
+        h->halo_recv[1][f] = h->ws + L.off_halo + (size_t)(3 * f + 2) * L.halo_bytes;
+    }
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -593,6 +643,10 @@ int lbms_step(lbms_t* h, long n_steps)
                     h->dirichlet & ~h->xb_set);
     if (h->relax == LBMS_RELAX_FROZEN && !h->xref_set)
         return fail(h, LBMS_EINVAL, "LBMS_RELAX_FROZEN needs lbms_set_reference first");
+    if (h->halo && n_steps > 1)
+        return fail(h, LBMS_EINVAL,
+                    "a slab with LBMS_HALO faces takes one step per call (its halos are exchanged "
+                    "between steps); use lbms_slab_step for several");
     h->err[0] = '\0';
     if (n_steps == 0) return LBMS_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -646,6 +700,8 @@ int moments_impl(lbms_t* h, void* x_sigma, void* J_sigma, void* G_sigma)
     KArgs a = base_args(h, h->stream);
     a.fin = h->steps > 0 ? h->f[1 - h->cur] : nullptr;
     a.fout = h->f[h->cur];
+    a.halo_recv[0] = h->halo_recv[1 - h->cur][0];
+    a.halo_recv[1] = h->halo_recv[1 - h->cur][1];
     const bool dev = (!x_sigma || is_device_ptr(x_sigma)) && (!J_sigma || is_device_ptr(J_sigma)) &&
                      (!G_sigma || is_device_ptr(G_sigma));
     cudaError_t e;
@@ -753,6 +809,7 @@ int lbms_get_state(lbms_t* h, void* f_out)
 int lbms_set_state_raw(lbms_t* h, const void* f_in, long step)
 {
     if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "a slab with LBMS_HALO faces is initialised by lbms_set_state only");
     if (!f_in) return fail(h, LBMS_EINVAL, "f_in is NULL");
     if (step < 0) return fail(h, LBMS_EINVAL, "step = %ld is negative", step);
     const size_t bytes = (size_t)h->S * h->Q * h->cells * h->es;
@@ -773,6 +830,7 @@ int lbms_set_state_raw(lbms_t* h, const void* f_in, long step)
 int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_out)
 {
     if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "lbms_recompute does not take LBMS_HALO faces");
     if (!f_in || !f_out) return fail(h, LBMS_EINVAL, "f_in and f_out must not be NULL");
     if (step < 0 || count < 0) return fail(h, LBMS_EINVAL, "step and count must not be negative");
     if (!is_device_ptr(f_in) || !is_device_ptr(f_out))
@@ -809,13 +867,14 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
 
 size_t lbms_adjoint_scratch_size(const lbms_t* h)
 {
-    if (!h || h->S > 4 || h->relax == LBMS_RELAX_FROZEN || !adjoint_lattice(h->lattice)) return 0;
+    if (!h || h->halo || h->S > 4 || h->relax == LBMS_RELAX_FROZEN || !adjoint_lattice(h->lattice)) return 0;
     return (size_t)node_blocks(h->cells) * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
 }
 
 int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
 {
     if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
@@ -833,6 +892,7 @@ int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
 int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* lam_out, void* gacc)
 {
     if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
@@ -854,6 +914,7 @@ int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* l
 int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
 {
     if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
@@ -871,6 +932,7 @@ int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
 int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
 {
     if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
     if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
@@ -896,6 +958,97 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
 long lbms_steps_done(const lbms_t* h) { return h ? h->steps : -1; }
 
 const void* lbms_populations(const lbms_t* h) { return h ? h->f[h->cur] : nullptr; }
+
+int lbms_set_subdomain(lbms_t* h, long first_layer)
+{
+    if (!h) return LBMS_EINVAL;
+    if (first_layer < 0) return fail(h, LBMS_EINVAL, "first_layer = %ld is negative", first_layer);
+    h->err[0] = '\0';
+    // node indices of the undivided grid (modulo 2^32, as the rounding key takes them)
+    h->origin = (uint32_t)((uint64_t)first_layer * h->plane);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 5; ++j)
+            if (h->graph[i][j]) {
+                cudaGraphExecDestroy(h->graph[i][j]);
+                h->graph[i][j] = nullptr;
+            }
+    return LBMS_OK;
+}
+
+int lbms_halo_buffers(lbms_t* h, int face, void** send, void** recv, size_t* bytes)
+{
+    if (!h) return LBMS_EINVAL;
+    if (face < 0 || face > 5 || !((h->halo >> face) & 1u))
+        return fail(h, LBMS_EINVAL, "face %d is not an LBMS_HALO face", face);
+    h->err[0] = '\0';
+    const int side = face & 1;
+    if (send) *send = h->halo_send[side];
+    if (recv) *recv = h->halo_recv[h->cur][side];
+    if (bytes) *bytes = (size_t)lattice_halo_width(h->lattice) * h->S * h->plane * h->es;
+    return LBMS_OK;
+}
+
+int lbms_slab_step(lbms_t* const* subs, int count, long n_steps)
+{
+    if (!subs || count < 1) return set_call_error(LBMS_EINVAL, "subs is NULL or count < 1");
+    for (int i = 0; i < count; ++i)
+        if (!subs[i]) return set_call_error(LBMS_EINVAL, "subs[%d] is NULL", i);
+    lbms_t* h0 = subs[0];
+    if (n_steps < 0) return fail(h0, LBMS_EINVAL, "n_steps = %ld is negative", n_steps);
+    const uint32_t lo_bit = 1u << (2 * (h0->dim - 1)), hi_bit = lo_bit << 1;
+    for (int i = 0; i < count; ++i) {
+        const lbms_t* h = subs[i];
+        if (h->lattice != h0->lattice || h->n != h0->n || h->dtype != h0->dtype || h->plane != h0->plane ||
+            h->nx != h0->nx || (h0->dim == 3 && h->ny != h0->ny))
+            return fail(h0, LBMS_EINVAL, "slab %d differs in lattice, species, dtype or layer shape", i);
+        if (h->stream != h0->stream) return fail(h0, LBMS_EINVAL, "slab %d is on another stream", i);
+        if (h->steps != h0->steps) return fail(h0, LBMS_EINVAL, "slab %d is at another step", i);
+        if (h->dirichlet & ~h->xb_set)
+            return fail(h0, LBMS_EINVAL, "slab %d: a Dirichlet face has no composition set", i);
+        if (h->relax == LBMS_RELAX_FROZEN && !h->xref_set)
+            return fail(h0, LBMS_EINVAL, "slab %d: LBMS_RELAX_FROZEN needs lbms_set_reference first", i);
+        // a cut is a pair of LBMS_HALO faces: this slab's high face and the next
+        // slab's low face (the last slab's high face pairs with the first's low
+        // face when the split axis wraps)
+        const lbms_t* up = subs[(i + 1) % count];
+        if (((h->halo & hi_bit) != 0) != ((up->halo & lo_bit) != 0))
+            return fail(h0, LBMS_EINVAL, "the faces between slab %d and slab %d are not a pair of cuts", i,
+                        (i + 1) % count);
+    }
+    h0->err[0] = '\0';
+    const size_t hb = (size_t)lattice_halo_width(h0->lattice) * h0->S * h0->plane * h0->es;
+    cudaStream_t st = h0->stream;
+    for (long t = 0; t < n_steps; ++t) {
+        // halo exchange: every slab's receive buffers of its current parity get
+        // the neighbours' populations that cross the cuts
+        for (int i = 0; i < count; ++i) {
+            lbms_t* h = subs[i];
+            cudaError_t e = cudaSuccess;
+            if (h->halo & hi_bit) {
+                lbms_t* up = subs[(i + 1) % count];
+                e = cudaMemcpyAsync(up->halo_recv[up->cur][0], h->halo_send[1], hb, cudaMemcpyDeviceToDevice, st);
+            }
+            if (e == cudaSuccess && (h->halo & lo_bit)) {
+                lbms_t* dn = subs[(i + count - 1) % count];
+                e = cudaMemcpyAsync(dn->halo_recv[dn->cur][1], h->halo_send[0], hb, cudaMemcpyDeviceToDevice, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(h0, e, "halo exchange");
+        }
+        const bool last = t + 1 == n_steps;
+        for (int i = 0; i < count; ++i) {
+            lbms_t* h = subs[i];
+            cudaError_t e = launch_step(h, h->cur, last, st);
+            if (e != cudaSuccess) return cuda_fail(h0, e, "step kernel");
+            h->cur = 1 - h->cur;
+            ++h->steps;
+            if (last) {
+                h->partials_valid = true;
+                h->mass_valid = false;
+            }
+        }
+    }
+    return LBMS_OK;
+}
 
 const char* lbms_last_error(const lbms_t* h) { return h ? h->err : g_create_error; }
 

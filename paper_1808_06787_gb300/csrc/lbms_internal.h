@@ -36,6 +36,11 @@ struct KArgs {
     uint32_t noflux = 0;                  // bit f set: face f is no-flux (x-, x+, y-, y+, z-, z+)
     uint32_t dirichlet = 0;               // bit f set: face f is Dirichlet (fixed composition)
     const void* xb = nullptr;             // Dirichlet compositions [6][S] in the solver's dtype
+    uint32_t halo = 0;                    // bit f set: face f is a slab cut (faces of the split axis)
+    uint32_t plane = 1;                   // nodes per layer of the split axis
+    uint32_t origin = 0;                  // global index of node 0 (slab offset; rounding key)
+    const void* halo_recv[2] = {nullptr, nullptr};  // receive buffers (low, high face) of the read parity
+    void* halo_send[2] = {nullptr, nullptr};        // send buffers (low, high face)
     int relax = LBMS_RELAX_MAGIC;
     int n_species = 2;
     double invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES] = {};  // 1 / D_ij

@@ -251,6 +251,9 @@ struct Geom {
     uint32_t nxy, cells;
     uint32_t noflux;     // bit f set: face f is a wall, no-flux or Dirichlet (x-, x+, y-, y+, z-, z+)
     uint32_t dirichlet;  // bit f set: wall face f holds a fixed composition
+    uint32_t halo;       // bit f set: face f is a cut of a slab decomposition (faces of the split axis)
+    uint32_t plane;      // nodes per layer of the split axis (nxy in 3D, nx in 2D, 1 in 1D)
+    uint32_t origin;     // global index of node 0 (a slab's offset in the undivided grid)
     FastDiv dnx, dny;
 };
 
@@ -259,7 +262,22 @@ struct Geom {
 struct Neighbourhood {
     int32_t ox[2], oy[2], oz[2];  // [0]: c = +1 (source at -1), [1]: c = -1 (source at +1)
     bool bx[2], by[2], bz[2];
-    uint32_t dir;  // the Dirichlet faces this node lies on (bits as Geom::noflux)
+    uint32_t dir;   // the Dirichlet faces this node lies on (bits as Geom::noflux)
+    uint32_t hal;   // the cut faces this node lies on (bits as Geom::noflux)
+    uint32_t inpl;  // the node's index within its layer of the split axis
+};
+
+// Receive and send buffers of the two cut faces of a slab (faces of the split
+// axis): [halo_width][S][plane] each, slot j of halo_slot.  recv_lo holds the
+// lower neighbour's populations that cross the cut upward, taken from its top
+// layer, recv_hi the upper neighbour's downward ones from its bottom layer;
+// send_hi / send_lo are this slab's own, written by every step.
+template <typename T>
+struct Halo {
+    const T* __restrict__ recv_lo;
+    const T* __restrict__ recv_hi;
+    T* send_lo;
+    T* send_hi;
 };
 
 // DIM is the lattice's dimension: a 2D grid has nz = 1 and a 1D grid ny = nz = 1,
@@ -299,8 +317,36 @@ __device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t c
     if (g.dirichlet)  // uniform over the grid
         h.dir = g.dirichlet & ((xlo ? 1u : 0u) | (xhi ? 2u : 0u) | (ylo ? 4u : 0u) |
                                (yhi ? 8u : 0u) | (zlo ? 16u : 0u) | (zhi ? 32u : 0u));
+    h.hal = 0u;
+    h.inpl = 0u;
+    if (g.halo) {  // uniform over the grid: a slab of a decomposed grid
+        // faces of the split axis that are cuts: the source across them is in a
+        // neighbour's receive buffer; the offsets along that axis are set to stay
+        // on the node (the gathered value is replaced)
+        if (DIM == 3) {
+            h.hal = g.halo & ((zlo ? 16u : 0u) | (zhi ? 32u : 0u));
+            if (h.hal & 16u) h.oz[0] = 0;
+            if (h.hal & 32u) h.oz[1] = 0;
+            h.inpl = cell - (uint32_t)z * g.nxy;
+        } else if (DIM == 2) {
+            h.hal = g.halo & ((ylo ? 4u : 0u) | (yhi ? 8u : 0u));
+            if (h.hal & 4u) h.oy[0] = 0;
+            if (h.hal & 8u) h.oy[1] = 0;
+            h.inpl = (uint32_t)x;
+        } else {
+            h.hal = g.halo & ((xlo ? 1u : 0u) | (xhi ? 2u : 0u));
+            if (h.hal & 1u) h.ox[0] = 0;
+            if (h.hal & 2u) h.ox[1] = 0;
+        }
+    }
     return h;
 }
+
+// Bits of the low and high cut faces of the split axis.
+template <int DIM>
+__host__ __device__ constexpr uint32_t halo_lo_bit() { return DIM == 3 ? 16u : (DIM == 2 ? 4u : 1u); }
+template <int DIM>
+__host__ __device__ constexpr uint32_t halo_hi_bit() { return DIM == 3 ? 32u : (DIM == 2 ? 8u : 2u); }
 
 // The wall face the pull source of direction k lies across, or -1.  A D2Q9
 // diagonal at a corner can cross two walls: the first in axis order x, y, z
@@ -327,10 +373,11 @@ __device__ __forceinline__ int link_wall(int k, const Neighbourhood& h)
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, uint32_t cell,
                                      const Neighbourhood& h, T (&f)[S][Lattice<LAT>::Q],
-                                     const T* __restrict__ xb)
+                                     const T* __restrict__ xb, const Halo<T>* halo = nullptr)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
+    constexpr int DIM = L::DIM;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
@@ -344,6 +391,27 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
 #pragma unroll
         for (int s = 0; s < S; ++s) f[s][k] = fin[(size_t)s * Q * g.cells + plane + src];
     }
+    if (halo && h.hal) {
+        // slab cut: a source across a cut face (and across no wall of another
+        // axis, which bounces first) is the neighbour's population in the
+        // receive buffer, at the source's position within the layer
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int c = split_c<LAT>(k);
+            if (c == 0) continue;
+            if (!(h.hal & (c > 0 ? halo_lo_bit<DIM>() : halo_hi_bit<DIM>()))) continue;
+            const int cx = L::cx(k), cy = L::cy(k);
+            bool bounce = false;
+            int32_t inoff = 0;
+            if (DIM >= 2 && cx != 0) { inoff += h.ox[cx > 0 ? 0 : 1]; bounce |= h.bx[cx > 0 ? 0 : 1]; }
+            if (DIM == 3 && cy != 0) { inoff += h.oy[cy > 0 ? 0 : 1]; bounce |= h.by[cy > 0 ? 0 : 1]; }
+            if (bounce) continue;
+            const T* rb = c > 0 ? halo->recv_lo : halo->recv_hi;
+            const uint32_t at = (uint32_t)((int32_t)h.inpl + inoff);
+#pragma unroll
+            for (int s = 0; s < S; ++s) f[s][k] = rb[((size_t)halo_slot<LAT>(k) * S + s) * g.plane + at];
+        }
+    }
     if (h.dir) {
 #pragma unroll
         for (int k = L::K0; k < Q; ++k) {
@@ -353,6 +421,25 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
                 for (int s = 0; s < S; ++s) f[s][k] = T(2.0 * L::w(k)) * xb[wf * S + s] - f[s][k];
             }
         }
+    }
+}
+
+// Slab cut: a node on a cut face also writes its post-collision populations
+// that leave through that face into the face's send buffer.
+template <int LAT, int S, typename T>
+__device__ __forceinline__ void pack_halo(const T (&f)[S][Lattice<LAT>::Q], const Geom& g,
+                                          const Neighbourhood& h, const Halo<T>& halo)
+{
+    using L = Lattice<LAT>;
+    constexpr int DIM = L::DIM;
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+        const int c = split_c<LAT>(k);
+        if (c == 0) continue;
+        if (!(h.hal & (c > 0 ? halo_hi_bit<DIM>() : halo_lo_bit<DIM>()))) continue;
+        T* sb = c > 0 ? halo.send_hi : halo.send_lo;
+#pragma unroll
+        for (int s = 0; s < S; ++s) sb[((size_t)halo_slot<LAT>(k) * S + s) * g.plane + h.inpl] = f[s][k];
     }
 }
 

@@ -26,7 +26,7 @@ LATTICES = {"D2Q5": 0, "D2Q9": 1, "D3Q7": 2, "D3Q15": 3, "D1Q3": 4, "D2Q4": 5, "
 DIMS = {"D2Q5": 2, "D2Q9": 2, "D3Q7": 3, "D3Q15": 3, "D1Q3": 1, "D2Q4": 2, "D3Q6": 3}
 Q_OF = {"D2Q5": 5, "D2Q9": 9, "D3Q7": 7, "D3Q15": 15, "D1Q3": 3, "D2Q4": 4, "D3Q6": 6}
 RELAX = {"magic": 0, "srt": 1, "frozen": 2}
-FACE = {"periodic": 0, "noflux": 1, "dirichlet": 2}
+FACE = {"periodic": 0, "noflux": 1, "dirichlet": 2, "halo": 3}
 DTYPES = {torch.float32: 0, torch.float64: 1}
 
 LBMS_OK = 0
@@ -50,6 +50,7 @@ EXPORTED = (
     "lbms_get_state", "lbms_set_state_raw", "lbms_recompute", "lbms_adjoint_scratch_size",
     "lbms_adjoint_seed",
     "lbms_adjoint_step", "lbms_adjoint_initial", "lbms_adjoint_reduce",
+    "lbms_set_subdomain", "lbms_halo_buffers", "lbms_slab_step",
 )
 BATCH_CANDIDATES = 7
 
@@ -127,6 +128,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_adjoint_initial.restype = I
         L.lbms_adjoint_reduce.argtypes = [P, P, P]
         L.lbms_adjoint_reduce.restype = I
+        L.lbms_set_subdomain.argtypes = [P, ctypes.c_long]
+        L.lbms_set_subdomain.restype = I
+        L.lbms_halo_buffers.argtypes = [P, I, P, P, P]
+        L.lbms_halo_buffers.restype = I
+        L.lbms_slab_step.argtypes = [P, I, ctypes.c_long]
+        L.lbms_slab_step.restype = I
         L.lbms_batch_workspace_size.argtypes = [I, I, I, P, I]
         L.lbms_batch_workspace_size.restype = SZ
         L.lbms_batch_create.argtypes = [P, I, I, I, P, P, I, P, I, P, SZ, P]
@@ -260,6 +267,26 @@ def lbms_destroy(h) -> None:
     load().lbms_destroy(h)
 
 
+def lbms_set_subdomain(h, first_layer: int) -> None:
+    _check(h, load().lbms_set_subdomain(h, int(first_layer)), "lbms_set_subdomain")
+
+
+def lbms_halo_buffers(h, face: int):
+    """(send address, receive address, bytes) of a cut face of a slab."""
+    send, recv, nbytes = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_size_t()
+    _check(h, load().lbms_halo_buffers(h, int(face), ctypes.byref(send), ctypes.byref(recv),
+                                       ctypes.byref(nbytes)), "lbms_halo_buffers")
+    return int(send.value), int(recv.value), int(nbytes.value)
+
+
+def lbms_slab_step(handles, n_steps: int) -> None:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    rc = load().lbms_slab_step(arr, len(handles), int(n_steps))
+    if rc != LBMS_OK:
+        first = handles[0] if handles else None
+        raise LbmsError("lbms_slab_step: %s (%s)" % (ERRORS.get(rc, rc), load().lbms_last_error(first).decode()))
+
+
 # --- convenience wrapper ---------------------------------------------------
 
 class Solver:
@@ -311,6 +338,27 @@ class Solver:
         """Composition (all n species) held on Dirichlet face ``face`` (0..5 as in
         ``bc``); applies to the steps issued after this call."""
         lbms_set_boundary(self._h, face, xi_b)
+
+    def set_subdomain(self, first_layer: int) -> None:
+        """Index of this slab's first layer along the split axis in the undivided
+        grid (slab decomposition; see ``slab.py``)."""
+        lbms_set_subdomain(self._h, first_layer)
+
+    def halo_buffers(self, face: int):
+        """(send, receive) views of cut face ``face`` (0..5 as in ``bc``): tensors
+        [halo width, n - 1, layer nodes] in the workspace.  The receive buffer is
+        the one the next step reads (it alternates with the population buffers)."""
+        send, recv, nbytes = lbms_halo_buffers(self._h, face)
+        base = self.workspace.data_ptr()
+        es = 8 if self.dtype == torch.float64 else 4
+        plane = {3: self.grid[0] * self.grid[1], 2: self.grid[0], 1: 1}[self.dim]
+        width = nbytes // (es * (self.n - 1) * plane)
+
+        def view(addr):
+            raw = self.workspace[addr - base: addr - base + nbytes]
+            return raw.view(self.dtype).view(width, self.n - 1, plane)
+
+        return view(send), view(recv)
 
     @property
     def field_shape(self):

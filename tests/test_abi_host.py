@@ -57,9 +57,14 @@ def test_workspace_size(lib, lat, q, dim, n, dtype, es):
     cells = grid[0] * grid[1] * grid[2]
     size = p.lbms_workspace_size(lat, n, grid, dtype)
     pop = (n - 1) * q * cells * es
-    assert size >= 2 * pop + n * (1 + dim) * cells * es
+    # halo buffers of the split axis: 6 x [crossing populations][S][layer nodes]
+    width = {0: 1, 1: 3, 2: 1, 3: 5, 4: 1, 5: 1, 6: 1}[lat]
+    layer = {3: grid[0] * grid[1], 2: grid[0], 1: 1}[dim]
+    halo = 6 * width * (n - 1) * layer * es
+    assert size >= 2 * pop + n * (1 + dim) * cells * es + halo
     assert size % 256 == 0
-    assert size < 2 * pop + n * (1 + dim) * cells * es + 64 * 1024 + cells * n * 16 // 256 + 4096
+    assert size < (2 * pop + n * (1 + dim) * cells * es + halo + 64 * 1024 + cells * n * 16 // 64
+                   + 8192)
 
 
 def test_workspace_size_rejects(lib):
@@ -97,8 +102,14 @@ def test_create_validates_before_device_work(lib):
     assert rc == 1
     rc, _, msg = _create(lib, bc=(0, 1, 0, 0, 0, 0))
     assert rc == 1 and "paired" in msg
-    rc, _, msg = _create(lib, bc=(3, 3, 0, 0, 0, 0))  # unknown face kind
+    rc, _, msg = _create(lib, bc=(4, 4, 0, 0, 0, 0))  # unknown face kind
     assert rc == 1 and "face kind" in msg
+    rc, _, msg = _create(lib, bc=(3, 3, 0, 0, 0, 0))  # slab cut on x: D2Q5 is split along y
+    assert rc == 1 and "split axis" in msg
+    rc, _, msg = _create(lib, bc=(0, 0, 3, 0, 0, 0))  # a cut paired with a periodic face
+    assert rc == 1 and "paired" in msg
+    rc, _, msg = _create(lib, lat=2, grid=(4, 4, 4), bc=(1, 1, 3, 3, 1, 1))  # D3Q7 is split along z
+    assert rc == 1 and "split axis" in msg
     rc, _, msg = _create(lib, bc=(2, 0, 0, 0, 0, 0))  # Dirichlet against a periodic face
     assert rc == 1 and "paired" in msg
     rc, _, msg = _create(lib, relax=3)
@@ -125,6 +136,9 @@ def test_null_handle_calls(lib):
     assert lib.lbms_status(None, None) == 1
     assert lib.lbms_steps_done(None) == -1
     assert lib.lbms_populations(None) is None
+    assert lib.lbms_set_subdomain(None, 0) == 1
+    assert lib.lbms_halo_buffers(None, 0, None, None, None) == 1
+    assert lib.lbms_slab_step(None, 0, 1) == 1
     lib.lbms_destroy(None)
 
 
@@ -151,7 +165,7 @@ def test_binding_constants_match_the_header():
     assert {"magic": h["LBMS_RELAX_MAGIC"], "srt": h["LBMS_RELAX_SRT"],
             "frozen": h["LBMS_RELAX_FROZEN"]} == b.RELAX
     assert {"periodic": h["LBMS_PERIODIC"], "noflux": h["LBMS_NOFLUX"],
-            "dirichlet": h["LBMS_DIRICHLET"]} == b.FACE
+            "dirichlet": h["LBMS_DIRICHLET"], "halo": h["LBMS_HALO"]} == b.FACE
     assert sorted(b.DTYPES.values()) == [h["LBMS_F32"], h["LBMS_F64"]]
     assert b.FLAG_NONFINITE == h["LBMS_FLAG_NONFINITE"]
     assert b.FLAG_RANGE == h["LBMS_FLAG_RANGE"]
