@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
     // the gather and scatter offsets depend on the geometry only: formed while
     // the previous step drains
     Neighbourhood h;
-    if (active) h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
+    if (active) h = neighbourhood<Lattice<LAT>::DIM, false>(p.g, cell);
     await_previous_grid();
     T dc[NP];
 #pragma unroll

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
     if (blk == d.block0 && threadIdx.x == 0) clk[1 - p.parity] = step + 1;
     T xi[S + 1];
     if (active) {
-        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(d.g, local);
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
         Geom plane = d.g;
         plane.cells = p.total_nodes;  // the gather's plane stride
         const uint32_t cell = d.base + local;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
 #pragma unroll
         for (int a = 0; a < DIM; ++a) J[s][a] = T(0);
     if (p.fin) {
-        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(d.g, local);
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
         Geom plane = d.g;
         plane.cells = p.total_nodes;
         T f[S][Q];

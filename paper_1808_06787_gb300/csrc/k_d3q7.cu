@@ -5,7 +5,8 @@ namespace lbms {
 
 cudaError_t dispatch_d3q7(Op op, int dtype, const KArgs& a)
 {
-    return dispatch_lattice<LBMS_D3Q7>(op, dtype, a);
+    if (slab_step_op(op, a)) return dispatch_halo_d3q7(op, dtype, a);
+    return dispatch_lattice<LBMS_D3Q7, false>(op, dtype, a);
 }
 
 }  // namespace lbms

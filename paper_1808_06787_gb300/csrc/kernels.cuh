@@ -192,7 +192,9 @@ struct StepOccupancy {
 // One time step: pull-stream (Eq. 3-13b, bounce-back/periodic faces), mole
 // fractions (Eq. 3-15), relaxation matrices (Eqs. 2-10, 3-26, 3-16), collision
 // (Eq. 3-13a with f_eq of Eq. 3-3) and store of the post-collision populations.
-template <int LAT, int S, typename T, bool MASS>
+// HALO: the grid is a slab with cut faces (slab decomposition); kernels of
+// undivided grids are compiled without the halo code.
+template <int LAT, int S, typename T, bool MASS, bool HALO>
 __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_step(StepParams<T> p)
 {
     using L = Lattice<LAT>;
@@ -204,9 +206,9 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.clock_out = step + 1;
     T xi[S + 1];
     if (active) {
-        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM>(p.g, cell);
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, HALO>(p.g, cell);
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb, &p.halo);
+        pull<LAT, S, T>(p.fin, p.g, cell, h, f, p.xb, HALO ? &p.halo : nullptr);
         mole_fractions<LAT, S, T>(f, xi);
         if (MASS) check_range<S, T>(xi, p.status);  // once per lbms_step call
         T L1[S][S], L2[S][S];
@@ -215,12 +217,13 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
         relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
         // the rounding key uses the node's index in the undivided grid, so that
         // the slabs of a decomposed grid round as the whole grid does
-        collide<LAT, S, T>(f, xi, L1, L2, mix32(step * 0x9e3779b9u) ^ ((cell + p.g.origin) * 0x27d4eb2du));
+        collide<LAT, S, T>(f, xi, L1, L2,
+                           mix32(step * 0x9e3779b9u) ^ ((HALO ? cell + p.g.origin : cell) * 0x27d4eb2du));
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.g.cells + cell] = f[s][k];
-        if (h.hal) pack_halo<LAT, S, T>(f, p.g, h, p.halo);
+        if (HALO && h.hal) pack_halo<LAT, S, T>(f, p.g, h, p.halo);
     }
     if (MASS) write_mass_partials<S>(xi, active, p.mass);
 }
@@ -405,7 +408,10 @@ inline Geom make_geom(const KArgs& a)
     return g;
 }
 
-template <int LAT, int S, typename T>
+// HALO_STEPS selects the step kernels of slabs (grids with cut faces): the
+// per-lattice translation units k_*.cu instantiate the others and kh_*.cu these,
+// so that the two halves compile in parallel.
+template <int LAT, int S, typename T, bool HALO_STEPS>
 cudaError_t launch(Op op, const KArgs& a)
 {
     if (op == OP_STEP || op == OP_STEP_MASS || op == OP_MASS) {
@@ -424,53 +430,69 @@ cudaError_t launch(Op op, const KArgs& a)
         p.co = make_coeffs<T>(a);
         const uint32_t tb = a.step_block;
         const uint32_t blocks = (a.cells + tb - 1) / tb;
-        if (op == OP_STEP) return launch_chained(k_step<LAT, S, T, false>, blocks, tb, a.stream, p);
-        if (op == OP_STEP_MASS) return launch_chained(k_step<LAT, S, T, true>, blocks, tb, a.stream, p);
-        k_mass<LAT, S, T><<<blocks, tb, 0, a.stream>>>(p);
+        if constexpr (HALO_STEPS) {
+            // slabs step one exchange at a time: every step writes the mass
+            // partials (one kernel variant instead of two)
+            if (op == OP_STEP || op == OP_STEP_MASS)
+                return launch_chained(k_step<LAT, S, T, true, true>, blocks, tb, a.stream, p);
+            return cudaErrorInvalidValue;
+        } else {
+            if (op == OP_STEP) return launch_chained(k_step<LAT, S, T, false, false>, blocks, tb, a.stream, p);
+            if (op == OP_STEP_MASS) return launch_chained(k_step<LAT, S, T, true, false>, blocks, tb, a.stream, p);
+            k_mass<LAT, S, T><<<blocks, tb, 0, a.stream>>>(p);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (HALO_STEPS) {
+        return cudaErrorInvalidValue;
+    } else {
+        FieldParams<T> p;
+        p.fprev = static_cast<const T*>(a.fin);
+        p.fcur = static_cast<T*>(a.fout);
+        p.x_in = static_cast<const T*>(a.field_in);
+        p.x_out = static_cast<T*>(a.field_x);
+        p.J_out = static_cast<T*>(a.field_J);
+        p.G_out = static_cast<T*>(a.field_G);
+        p.g = make_geom(a);
+        p.c0 = a.c0; p.c1 = a.c1; p.stride = a.stride;
+        p.relax = a.relax;
+        p.status = a.status;
+        p.xb = static_cast<const T*>(a.xb);
+        p.halo = make_halo<T>(a);
+        p.co = make_coeffs<T>(a);
+        const uint32_t blocks = node_blocks(a.c1 - a.c0);
+        if (blocks == 0) return cudaSuccess;
+        if (op == OP_INIT)
+            k_init<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p);
+        else
+            k_moments<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p);
         return cudaGetLastError();
     }
-    FieldParams<T> p;
-    p.fprev = static_cast<const T*>(a.fin);
-    p.fcur = static_cast<T*>(a.fout);
-    p.x_in = static_cast<const T*>(a.field_in);
-    p.x_out = static_cast<T*>(a.field_x);
-    p.J_out = static_cast<T*>(a.field_J);
-    p.G_out = static_cast<T*>(a.field_G);
-    p.g = make_geom(a);
-    p.c0 = a.c0; p.c1 = a.c1; p.stride = a.stride;
-    p.relax = a.relax;
-    p.status = a.status;
-    p.xb = static_cast<const T*>(a.xb);
-    p.halo = make_halo<T>(a);
-    p.co = make_coeffs<T>(a);
-    const uint32_t blocks = node_blocks(a.c1 - a.c0);
-    if (blocks == 0) return cudaSuccess;
-    if (op == OP_INIT)
-        k_init<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p);
-    else
-        k_moments<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p);
-    return cudaGetLastError();
 }
 
-template <int LAT, typename T>
+template <int LAT, typename T, bool HALO_STEPS>
 cudaError_t dispatch_S(Op op, const KArgs& a)
 {
     switch (a.n_species - 1) {
-        case 1: return launch<LAT, 1, T>(op, a);
-        case 2: return launch<LAT, 2, T>(op, a);
-        case 3: return launch<LAT, 3, T>(op, a);
-        case 4: return launch<LAT, 4, T>(op, a);
-        case 5: return launch<LAT, 5, T>(op, a);
-        case 6: return launch<LAT, 6, T>(op, a);
-        case 7: return launch<LAT, 7, T>(op, a);
+        case 1: return launch<LAT, 1, T, HALO_STEPS>(op, a);
+        case 2: return launch<LAT, 2, T, HALO_STEPS>(op, a);
+        case 3: return launch<LAT, 3, T, HALO_STEPS>(op, a);
+        case 4: return launch<LAT, 4, T, HALO_STEPS>(op, a);
+        case 5: return launch<LAT, 5, T, HALO_STEPS>(op, a);
+        case 6: return launch<LAT, 6, T, HALO_STEPS>(op, a);
+        case 7: return launch<LAT, 7, T, HALO_STEPS>(op, a);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int LAT>
+template <int LAT, bool HALO_STEPS>
 cudaError_t dispatch_lattice(Op op, int dtype, const KArgs& a)
 {
-    return dtype == LBMS_F64 ? dispatch_S<LAT, double>(op, a) : dispatch_S<LAT, float>(op, a);
+    return dtype == LBMS_F64 ? dispatch_S<LAT, double, HALO_STEPS>(op, a)
+                             : dispatch_S<LAT, float, HALO_STEPS>(op, a);
 }
+
+// Whether an operation runs a slab's step kernels (kh_*.cu).
+inline bool slab_step_op(Op op, const KArgs& a) { return a.halo && (op == OP_STEP || op == OP_STEP_MASS); }
 
 }  // namespace lbms

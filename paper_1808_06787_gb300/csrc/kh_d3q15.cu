@@ -1,0 +1,12 @@
+// Step kernels of slabs (grids with cut faces) for the D3Q15 lattice (all S = 1..7,
+// float and double).
+#include "kernels.cuh"
+
+namespace lbms {
+
+cudaError_t dispatch_halo_d3q15(Op op, int dtype, const KArgs& a)
+{
+    return dispatch_lattice<LBMS_D3Q15, true>(op, dtype, a);
+}
+
+}  // namespace lbms

@@ -998,8 +998,9 @@ int lbms_slab_step(lbms_t* const* subs, int count, long n_steps)
     const uint32_t lo_bit = 1u << (2 * (h0->dim - 1)), hi_bit = lo_bit << 1;
     for (int i = 0; i < count; ++i) {
         const lbms_t* h = subs[i];
+        // the extents across the split axis (the layer shape) must agree
         if (h->lattice != h0->lattice || h->n != h0->n || h->dtype != h0->dtype || h->plane != h0->plane ||
-            h->nx != h0->nx || (h0->dim == 3 && h->ny != h0->ny))
+            (h0->dim >= 2 && h->nx != h0->nx) || (h0->dim == 3 && h->ny != h0->ny))
             return fail(h0, LBMS_EINVAL, "slab %d differs in lattice, species, dtype or layer shape", i);
         if (h->stream != h0->stream) return fail(h0, LBMS_EINVAL, "slab %d is on another stream", i);
         if (h->steps != h0->steps) return fail(h0, LBMS_EINVAL, "slab %d is at another step", i);

@@ -62,6 +62,15 @@ cudaError_t dispatch_d3q15(Op op, int dtype, const KArgs& a);
 cudaError_t dispatch_d1q3(Op op, int dtype, const KArgs& a);
 cudaError_t dispatch_d2q4(Op op, int dtype, const KArgs& a);
 cudaError_t dispatch_d3q6(Op op, int dtype, const KArgs& a);
+// The step kernels of slabs (cut faces), one translation unit per lattice
+// (kh_*.cu); the dispatchers above forward to them.
+cudaError_t dispatch_halo_d2q5(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_halo_d2q9(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_halo_d3q7(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_halo_d3q15(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_halo_d1q3(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_halo_d2q4(Op op, int dtype, const KArgs& a);
+cudaError_t dispatch_halo_d3q6(Op op, int dtype, const KArgs& a);
 
 // Number of blocks a node kernel over `cells` nodes is launched with.
 inline uint32_t node_blocks(uint32_t cells) { return (cells + kBlock - 1) / kBlock; }

@@ -282,7 +282,7 @@ struct Halo {
 
 // DIM is the lattice's dimension: a 2D grid has nz = 1 and a 1D grid ny = nz = 1,
 // so those coordinates need no division.
-template <int DIM>
+template <int DIM, bool HALO = true>
 __device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t cell)
 {
     uint32_t row = 0;
@@ -319,7 +319,7 @@ __device__ __forceinline__ Neighbourhood neighbourhood(const Geom& g, uint32_t c
                                (yhi ? 8u : 0u) | (zlo ? 16u : 0u) | (zhi ? 32u : 0u));
     h.hal = 0u;
     h.inpl = 0u;
-    if (g.halo) {  // uniform over the grid: a slab of a decomposed grid
+    if (HALO && g.halo) {  // uniform over the grid: a slab of a decomposed grid
         // faces of the split axis that are cuts: the source across them is in a
         // neighbour's receive buffer; the offsets along that axis are set to stay
         // on the node (the gathered value is replaced)
