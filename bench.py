@@ -417,10 +417,60 @@ def single_line(wl: Workload, m: dict, steps: int, world: int, t_ms: float, sms:
     }
 
 
+def _split(wl: Workload) -> int:
+    from paper_1808_06787_gb300.slab import split_axis
+
+    return split_axis(wl.lattice)
+
+
 def device_sms(local: int) -> int:
     import torch
 
     return int(torch.cuda.get_device_properties(local).multi_processor_count)
+
+
+def sharded_grid(wl: Workload, world: int):
+    """Global grid of the sharded solve: every rank owns one workload-sized slab,
+    stacked along the lattice's split axis (weak scaling)."""
+    from paper_1808_06787_gb300.slab import split_axis
+
+    g = list(wl.grid)
+    g[split_axis(wl.lattice)] *= world
+    return tuple(g)
+
+
+def measure_sharded(wl: Workload, steps: int, warmup: int, dist, barrier, keep=False):
+    """Time `steps` steps of one grid sharded over the ranks (slab decomposition,
+    one slab per GPU, halo exchange by point-to-point messages every step).  Each
+    rank's slab is the workload's grid and holds the workload's initial field, so
+    the global field is the workload's field repeated along the split axis
+    (continuous for the x-only two-bulb profile and the periodic fields)."""
+    import numpy as np
+    import torch
+
+    from paper_1808_06787_gb300 import DistSlabSolver
+
+    tdtype = torch.float64 if wl.f64 else torch.float32
+    x0_host = torch.from_numpy(wl.x0()).to(tdtype).pin_memory()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = DistSlabSolver(wl.lattice, wl.D(), sharded_grid(wl, dist.get_world_size()), dist, bc=wl.bc,
+                           dtype=tdtype, stream=stream)
+        s.set_state(x0_host.cuda(non_blocking=True))
+        mass0 = s.mass()
+        s.step(warmup)
+        torch.cuda.synchronize()
+        ms, reps = timed_repeats(s.step, stream, steps, barrier)
+        flags = s.status()
+        mass = s.mass()
+    out = {"ms": ms, "repeats_ms": reps, "status_flags": flags,
+           "mass_drift_rel": float(np.max(np.abs(mass - mass0) / np.abs(mass0))),
+           "x0_host": x0_host, "stream": stream}
+    if keep:
+        out["solver"] = s
+    else:
+        s.close()
+    return out
 
 
 def run_ours(args, wl: Workload):
@@ -437,14 +487,18 @@ def run_ours(args, wl: Workload):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    m = measure_single(wl, args.steps, args.warmup, barrier, keep=True)
+    if world > 1:
+        m = measure_sharded(wl, args.steps, args.warmup, dist, barrier, keep=True)
+    else:
+        m = measure_single(wl, args.steps, args.warmup, barrier, keep=True)
     clocks = sampler.stop()
     s, stream, x0_host = m["solver"], m["stream"], m["x0_host"]
     tdtype = x0_host.dtype
 
     # end to end through the public API with host buffers: pinned x0 in,
     # K steps, mole fractions and masses back to pinned host memory
-    x_host = torch.empty(s.field_shape, dtype=tdtype).pin_memory()
+    field_shape = s.solver.field_shape if world > 1 else s.field_shape
+    x_host = torch.empty(field_shape, dtype=tdtype).pin_memory()
     e2e_s = None
     if not args.no_e2e:
         with torch.cuda.stream(stream):
@@ -452,7 +506,10 @@ def run_ours(args, wl: Workload):
             t0 = time.perf_counter()
             s.set_state(x0_host)
             s.step(args.steps)
-            s.moments(x_host)
+            if world > 1:
+                x_host.copy_(s.moments())
+            else:
+                s.moments(x_host)
             s.mass()
             barrier()
             e2e_s = time.perf_counter() - t0
@@ -489,8 +546,12 @@ def run_ours(args, wl: Workload):
                                                       "line": "two-bulb tanh profile",
                                                       "blobs": "Gaussian blobs",
                                                       "sine": "sine modes"}[wl.key],
-        "config": dict(line["config"], parallelism="replicas" if world > 1 else "single GPU",
-                       timing="median of %d repeats of the %d-step region (CUDA events)"
+        "config": dict(line["config"],
+                       parallelism=("slab decomposition: grid %s split along %s into %d slabs of %s, one "
+                                    "per GPU; one halo exchange per step (point-to-point), masses by one "
+                                    "all-reduce" % (list(sharded_grid(wl, world)), "xyz"[_split(wl)], world,
+                                                    list(wl.grid))) if world > 1 else "single GPU",
+                       timing="median of %d repeats of the %d-step region (CUDA events, max over ranks)"
                               % (line["repeats"], args.steps)),
         "roofline": line["roofline"],
         "e2e": None if args.no_e2e else {

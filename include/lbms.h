@@ -315,6 +315,14 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
  *   lbms_adjoint_step     lambda(t-1) from lambda(t) (lam_in != lam_out), given
  *                         the forward populations f+(t-1) of that step;
  *                         accumulates dL/d(1/D) into gacc.
+ *   lbms_adjoint_steps    `count` adjoint steps in one call (a segment of a
+ *                         checkpointed backward sweep): with f_first = f+(t0)
+ *                         and f_rest + j S Q cells = f+(t0 + 1 + j), j = 0 ..
+ *                         count - 2 (unused for count <= 1), the steps run from
+ *                         t0 + count down to t0 + 1; lambda(t0 + count) is read
+ *                         from lam_a and the buffers alternate, so lambda(t0)
+ *                         ends in lam_a for even count and in lam_b for odd.
+ *                         Same result as `count` calls of lbms_adjoint_step.
  *   lbms_adjoint_initial  dL/dx0 ([n][cells]) from lambda(0) (f+(0) = w_k x0);
  *                         the closure species does not enter the model and
  *                         gets zero.
@@ -325,6 +333,8 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
 size_t lbms_adjoint_scratch_size(const lbms_t* h);
 int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam);
 int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* lam_out, void* gacc);
+int lbms_adjoint_steps(lbms_t* h, const void* f_first, const void* f_rest, int count, void* lam_a, void* lam_b,
+                       void* gacc);
 int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0);
 int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD);
 

@@ -911,6 +911,38 @@ int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* l
     return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "adjoint step kernel");
 }
 
+int lbms_adjoint_steps(lbms_t* h, const void* f_first, const void* f_rest, int count, void* lam_a, void* lam_b,
+                       void* gacc)
+{
+    if (!h) return LBMS_EINVAL;
+    if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
+    if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
+    if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
+    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
+    if (count < 0) return fail(h, LBMS_EINVAL, "count = %d is negative", count);
+    if (!f_first || !lam_a || !lam_b || !gacc || (count > 1 && !f_rest))
+        return fail(h, LBMS_EINVAL, "f_first, f_rest (count > 1), lam_a, lam_b and gacc must not be NULL");
+    if (lam_a == lam_b) return fail(h, LBMS_EINVAL, "lam_a and lam_b must be different buffers");
+    if (!is_device_ptr(f_first) || (count > 1 && !is_device_ptr(f_rest)) || !is_device_ptr(lam_a) ||
+        !is_device_ptr(lam_b) || !is_device_ptr(gacc))
+        return fail(h, LBMS_EINVAL, "f_first, f_rest, lam_a, lam_b and gacc must be device memory");
+    h->err[0] = '\0';
+    const size_t fbytes = (size_t)h->S * h->Q * h->cells * h->es;
+    AArgs a;
+    a.k = base_args(h, h->stream);
+    a.gacc = static_cast<double*>(gacc);
+    // step t0 + count - i (i = 0 .. count - 1) reads f+(t0 + count - i - 1)
+    for (int i = 0; i < count; ++i) {
+        const int j = count - 1 - i;  // f+(t0 + j)
+        a.fprev = j == 0 ? f_first : static_cast<const char*>(f_rest) + (size_t)(j - 1) * fbytes;
+        a.lam_in = (i & 1) ? lam_b : lam_a;
+        a.lam_out = (i & 1) ? lam_a : lam_b;
+        cudaError_t e = adj_dispatch(h, AOP_STEP, a);
+        if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step kernel");
+    }
+    return LBMS_OK;
+}
+
 int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
 {
     if (!h) return LBMS_EINVAL;

@@ -49,7 +49,7 @@ EXPORTED = (
     "lbms_batch_last_error", "lbms_batch_destroy",
     "lbms_get_state", "lbms_set_state_raw", "lbms_recompute", "lbms_adjoint_scratch_size",
     "lbms_adjoint_seed",
-    "lbms_adjoint_step", "lbms_adjoint_initial", "lbms_adjoint_reduce",
+    "lbms_adjoint_step", "lbms_adjoint_steps", "lbms_adjoint_initial", "lbms_adjoint_reduce",
     "lbms_set_subdomain", "lbms_halo_buffers", "lbms_slab_step",
 )
 BATCH_CANDIDATES = 7
@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_adjoint_seed.restype = I
         L.lbms_adjoint_step.argtypes = [P, P, P, P, P]
         L.lbms_adjoint_step.restype = I
+        L.lbms_adjoint_steps.argtypes = [P, P, P, I, P, P, P]
+        L.lbms_adjoint_steps.restype = I
         L.lbms_adjoint_initial.argtypes = [P, P, P]
         L.lbms_adjoint_initial.restype = I
         L.lbms_adjoint_reduce.argtypes = [P, P, P]
@@ -469,6 +471,17 @@ class Solver:
                                                  ctypes.c_void_p(lam_in.data_ptr()),
                                                  ctypes.c_void_p(lam_out.data_ptr()),
                                                  ctypes.c_void_p(gacc.data_ptr())), "lbms_adjoint_step")
+
+    def adjoint_steps(self, f_first: torch.Tensor, f_rest: Optional[torch.Tensor], count: int,
+                      lam_a: torch.Tensor, lam_b: torch.Tensor, gacc: torch.Tensor) -> None:
+        """``count`` adjoint steps of a segment in one call (lbms_adjoint_steps):
+        forward states f_first = f+(t0) and f_rest[j] = f+(t0 + 1 + j); lambda
+        starts in lam_a and ends in lam_a (even count) or lam_b (odd count)."""
+        rest = ctypes.c_void_p(f_rest.data_ptr()) if f_rest is not None else None
+        _check(self._h, load().lbms_adjoint_steps(self._h, ctypes.c_void_p(f_first.data_ptr()), rest,
+                                                  int(count), ctypes.c_void_p(lam_a.data_ptr()),
+                                                  ctypes.c_void_p(lam_b.data_ptr()),
+                                                  ctypes.c_void_p(gacc.data_ptr())), "lbms_adjoint_steps")
 
     def adjoint_initial(self, lam0: torch.Tensor) -> torch.Tensor:
         out = torch.empty(self.field_shape, dtype=self.dtype, device=self.device)

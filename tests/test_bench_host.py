@@ -105,3 +105,10 @@ def test_fp64_peak_follows_sm_count_and_sampled_clock():
     r = bench.fp64_roofline(wl, 0.006, 148, 1900.0)
     assert r["peak"] == pytest.approx(148 * 2 * 2 * 1.9e9 / 1e12, rel=1e-3)
     assert "148 SMs" in r["peak_source"] and "1900 MHz" in r["peak_source"]
+
+
+def test_sharded_grid_stacks_one_workload_grid_per_rank():
+    assert bench.sharded_grid(bench.make_workload("tube", 256), 4) == (256, 256, 1024)
+    assert bench.sharded_grid(bench.make_workload("blobs", 256), 2) == (2048, 4096, 1)
+    assert bench.sharded_grid(bench.make_workload("line", 256), 8) == (8 << 26, 1, 1)
+    assert bench.sharded_grid(bench.make_workload("tube", 256), 1) == (256, 256, 256)

@@ -386,3 +386,38 @@ def test_adjoint_entry_points_refuse_host_buffers():
     s.adjoint_seed(torch.ones(s.field_shape, dtype=torch.float64, device="cuda"), lam)
     s.adjoint_step(f, lam, lam2, gacc)
     assert np.all(np.isfinite(s.adjoint_reduce(gacc)))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_adjoint_steps_equal_single_adjoint_steps(dtype, count):
+    """lbms_adjoint_steps (a segment in one call) = `count` calls of
+    lbms_adjoint_step, bit for bit, including the gradient accumulator."""
+    from paper_1808_06787_gb300 import Solver
+
+    n, dims = 3, (23, 17, 1)
+    s = Solver("D2Q5", sy.random_D(n, seed=91), dims, bc=(W, W, P, P, P, P), dtype=dtype)
+    s.set_state(torch.from_numpy(sy.sin_modes(n, *dims, amp=0.1, seed=92)).to(dtype).cuda())
+    s.step(3)
+    states = [s.get_state()]
+    for _ in range(count - 1):
+        s.step(1)
+        states.append(s.get_state())
+    rest = torch.stack(states[1:]) if count > 1 else None
+    g = torch.Generator(device="cpu").manual_seed(93)
+    seed_x = (1e-2 * torch.randn(s.field_shape, generator=g, dtype=torch.float64)).to(dtype).cuda()
+    lam0 = s.adjoint_state()
+    s.adjoint_seed(seed_x, lam0)
+    # reference: single steps from the last state back to the first
+    a, b = lam0.clone(), s.adjoint_state()
+    ga = s.adjoint_scratch()
+    for j in range(count - 1, -1, -1):
+        s.adjoint_step(states[j], a, b, ga)
+        a, b = b, a
+    # one call
+    la, lb = lam0.clone(), s.adjoint_state()
+    gb = s.adjoint_scratch()
+    s.adjoint_steps(states[0], rest, count, la, lb, gb)
+    out = lb if count % 2 else la
+    assert torch.equal(out, a)
+    assert torch.equal(gb, ga)
