@@ -38,11 +38,14 @@ __host__ __device__ constexpr int pair_index(int p, int q, int S)
     return p * (2 * (S + 1) - p - 1) / 2 + (q - p - 1);
 }
 
-template <int LAT, int S, typename T, typename InvD>
+// The adjoint of one node's collision.  mu(s, k) is handed to emit(s, k, value)
+// as soon as it is known (the scatter store in the step kernel): a first pass
+// over the pairs accumulates H and sum_k w_k nu_k, a second forms mu, so that the
+// populations f are dead before mu is formed and no mu array is held.
+template <int LAT, int S, typename T, typename InvD, typename Emit>
 __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
                                              const T (&lam)[S][Lattice<LAT>::Q], const InvD& invD,
-                                             T cs2inv, int relax, T (&mu)[S][Lattice<LAT>::Q],
-                                             T (&dc)[NPairs<S>::value])
+                                             T cs2inv, int relax, T (&dc)[NPairs<S>::value], Emit&& emit)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
@@ -67,24 +70,39 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
             K[i][j] = T(0.5) * b + (i == j ? cs2inv : T(0));
             Ki[i][j] = i == j ? T(1) : T(0);
         }
+    if constexpr (S == 2) {
+        // ternary mixtures: K^{-1} = adj(K) / det(K) with one reciprocal, and
+        // Lambda_1 = K^{-1} B (det(K) > 0: B's eigenvalues are real, >= 0)
+        const T rdet = recip(K[0][0] * K[1][1] - K[0][1] * K[1][0]);
+        Ki[0][0] = K[1][1] * rdet;
+        Ki[0][1] = -K[0][1] * rdet;
+        Ki[1][0] = -K[1][0] * rdet;
+        Ki[1][1] = K[0][0] * rdet;
+        const T b00 = L1[0][0], b01 = L1[0][1], b10 = L1[1][0], b11 = L1[1][1];
+        L1[0][0] = Ki[0][0] * b00 + Ki[0][1] * b10;
+        L1[0][1] = Ki[0][0] * b01 + Ki[0][1] * b11;
+        L1[1][0] = Ki[1][0] * b00 + Ki[1][1] * b10;
+        L1[1][1] = Ki[1][0] * b01 + Ki[1][1] * b11;
+    } else {
 #pragma unroll
-    for (int p = 0; p < S; ++p) {
-        const T inv = recip(K[p][p]);
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            K[p][j] *= inv;
-            L1[p][j] *= inv;
-            Ki[p][j] *= inv;
-        }
-#pragma unroll
-        for (int r = 0; r < S; ++r) {
-            if (r == p) continue;
-            const T fac = K[r][p];
+        for (int p = 0; p < S; ++p) {
+            const T inv = recip(K[p][p]);
 #pragma unroll
             for (int j = 0; j < S; ++j) {
-                K[r][j] -= fac * K[p][j];
-                L1[r][j] -= fac * L1[p][j];
-                Ki[r][j] -= fac * Ki[p][j];
+                K[p][j] *= inv;
+                L1[p][j] *= inv;
+                Ki[p][j] *= inv;
+            }
+#pragma unroll
+            for (int r = 0; r < S; ++r) {
+                if (r == p) continue;
+                const T fac = K[r][p];
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    K[r][j] -= fac * K[p][j];
+                    L1[r][j] -= fac * L1[p][j];
+                    Ki[r][j] -= fac * Ki[p][j];
+                }
             }
         }
     }
@@ -94,15 +112,30 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
 #pragma unroll
         for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
         rp[i] = T(1);
-        if (relax == LBMS_RELAX_MAGIC) {
-            const T l = L1[i][i];
-            const T r8 = recip(l - T(8));
-            L2[i][i] = T(8) * (l - T(2)) * r8;  // Eq. 3-16
-            rp[i] = T(-48) * r8 * r8;           // its derivative
+    }
+    if (relax == LBMS_RELAX_MAGIC) {
+        if constexpr (S == 2) {
+            // Eq. 3-16 and its derivative for both diagonal entries, one reciprocal
+            const T a = L1[0][0] - T(8), b = L1[1][1] - T(8);
+            const T r = recip(a * b);
+            const T r8a = b * r, r8b = a * r;  // 1 / (l - 8) of each entry
+            L2[0][0] = T(8) * (L1[0][0] - T(2)) * r8a;
+            L2[1][1] = T(8) * (L1[1][1] - T(2)) * r8b;
+            rp[0] = T(-48) * r8a * r8a;
+            rp[1] = T(-48) * r8b * r8b;
+        } else {
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const T l = L1[i][i];
+                const T r8 = recip(l - T(8));
+                L2[i][i] = T(8) * (l - T(2)) * r8;  // Eq. 3-16
+                rp[i] = T(-48) * r8 * r8;           // its derivative
+            }
         }
     }
     // (a) Lambda fixed: nu = Omega^T lambda, mu = lambda - nu + sum_k w_k nu_k
     // (b) accumulators H = <lambda, odd(g)> + <lambda, even(g)> r
+    // first pass: H and wnu = sum_k w_k nu_k
     T Ga[S][S], Gs[S][S], wnu[S];
 #pragma unroll
     for (int i = 0; i < S; ++i)
@@ -116,7 +149,6 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
         T nu0 = T(0);
 #pragma unroll
         for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
-        mu[j][0] = lam[j][0] - nu0;
         wnu[j] = T(L::w(0)) * nu0;
     }
 #pragma unroll
@@ -133,14 +165,9 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
         }
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            T ns = T(0), na = T(0);
+            T ns = T(0);
 #pragma unroll
-            for (int i = 0; i < S; ++i) {
-                ns += L2[i][j] * ls[i];
-                na += L1[i][j] * la[i];
-            }
-            mu[j][ka] = lam[j][ka] - (ns + na);
-            mu[j][kb] = lam[j][kb] - (ns - na);
+            for (int i = 0; i < S; ++i) ns += L2[i][j] * ls[i];
             wnu[j] += T(2) * wp * ns;
         }
 #pragma unroll
@@ -173,6 +200,7 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
             Z[a][b] = acc;
         }
     // (b) s_m with E_m = dB/dxi_m (closure included), added to every population of m
+    T add[S];
 #pragma unroll
     for (int m = 0; m < S; ++m) {
         T s = T(0);
@@ -182,9 +210,7 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
 #pragma unroll
         for (int i = 0; i < S; ++i)
             if (i != m) s += (invD[i][m] - invD[i][S]) * Z[i][i];
-        const T add = wnu[m] - s;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) mu[m][k] += add;
+        add[m] = wnu[m] - s;
     }
     // dL/dc_pq with F_pq = dB/dc_pq
 #pragma unroll
@@ -200,6 +226,36 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
             // F[p][p] = xi_q, F[q][q] = xi_p
             dc[pair_index(p, q, S)] +=
                 -(-xi[p] * Z[p][q] - xi[q] * Z[q][p] + xi[q] * Z[p][p] + xi[p] * Z[q][q]);
+        }
+    }
+    // second pass: mu = lambda - nu + add, nu of the rest population and of the
+    // odd (Lambda_1) and even (Lambda_2) parts of every pair
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        T nu0 = T(0);
+#pragma unroll
+        for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
+        emit(j, 0, lam[j][0] - nu0 + add[j]);
+    }
+#pragma unroll
+    for (int pr = 0; pr < L::NPAIR; ++pr) {
+        const int ka = 2 * pr + 1, kb = 2 * pr + 2;
+        T ls[S], la[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            ls[i] = T(0.5) * (lam[i][ka] + lam[i][kb]);
+            la[i] = T(0.5) * (lam[i][ka] - lam[i][kb]);
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            T ns = T(0), na = T(0);
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                ns += L2[i][j] * ls[i];
+                na += L1[i][j] * la[i];
+            }
+            emit(j, ka, lam[j][ka] - (ns + na) + add[j]);
+            emit(j, kb, lam[j][kb] - (ns - na) + add[j]);
         }
     }
 }
@@ -266,27 +322,23 @@ struct LamIO<double> {
 
 // Adds the sum of v over the warp (all lanes taking part) to the warp's
 // accumulator slot, from lane 0.  FP32 solvers keep the slot as a float pair
-// (hi, lo) and sum with two-sums, on the FP32 pipes only: on GB300 an FP64
-// instruction occupies the narrow FP64 pipe for a whole warp even with one
-// active lane.  FP64 solvers keep a double.
+// (hi, lo) and add the warp's sum to it with a two-sum, on the FP32 pipes only:
+// on GB300 an FP64 instruction occupies the narrow FP64 pipe for a whole warp
+// even with one active lane.  The 32 terms of one warp come from 32
+// neighbouring nodes of one step, which hardly cancel (the strong cancellation
+// is between distant nodes and between steps, which the float-pair slot
+// carries), so the warp's own sum is a plain FP32 sum.  FP64 solvers keep a
+// double.
 __device__ __forceinline__ void warp_accumulate(float v, double* slot)
 {
-    float c = 0.0f;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ov = __shfl_down_sync(0xffffffffu, v, off);
-        const float oc = __shfl_down_sync(0xffffffffu, c, off);
-        float s, e;
-        two_sum(v, ov, s, e);
-        v = s;
-        c += e + oc;
-    }
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) {
         float2* acc = reinterpret_cast<float2*>(slot);
         const float2 a = *acc;
         float s, e;
         two_sum(a.x, v, s, e);
-        e += a.y + c;
+        e += a.y;
         const float hi = s + e;  // |e| is below an ulp of s: renormalise
         *acc = make_float2(hi, e - (hi - s));
     }
@@ -338,7 +390,7 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
 #pragma unroll
     for (int q = 0; q < NP; ++q) dc[q] = T(0);
     if (active) {
-        T f[S][Q], d[S][Q], mud[S][Q], lbar[S];
+        T f[S][Q], d[S][Q], lbar[S];
         pull<LAT, S, T>(p.fprev, p.g, cell, h, f, p.xb);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -353,11 +405,10 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
 #pragma unroll
             for (int k = 0; k < Q; ++k) d[s][k] = (hi[k] - acc) + lo[k];
         }
-        adjoint_node<LAT, S, T>(f, d, p.co.invD, T(1.0 / L::cs2()), p.relax, mud, dc);
-        // scatter through the gather's source slots; an anti-bounce-back link
-        // (Dirichlet face) entered the forward map with a factor -1
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        // scatter through the gather's source slots as each mu is formed; an
+        // anti-bounce-back link (Dirichlet face) entered the forward map with a
+        // factor -1
+        auto emit = [&](int s, int k, T mu) {
             const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
             int32_t off = 0;
             bool bounce = false;
@@ -371,10 +422,9 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
                 const int wf = link_wall<LAT>(k, h);
                 neg = wf >= 0 && ((h.dir >> wf) & 1u);
             }
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                IO::store(p.lam_out, (size_t)s * Q * p.g.cells + plane + dst, lbar[s], mud[s][k], neg);
-        }
+            IO::store(p.lam_out, (size_t)s * Q * p.g.cells + plane + dst, lbar[s], mu, neg);
+        };
+        adjoint_node<LAT, S, T>(f, d, p.co.invD, T(1.0 / L::cs2()), p.relax, dc, emit);
     }
     // warp sums of dL/dc (the contributions of different nodes and steps cancel
     // strongly), accumulated over steps in FP64 in the warp's own slot

@@ -109,6 +109,68 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
     if (MASS) write_mass_partials<S>(xi, active, p.mass);
 }
 
+// Two nodes per thread, as k_step_pair: blocks of kBlock / 2 threads cover one
+// kBlock-node block of one instance; the pair's rest populations come in one
+// load and every plane goes out in one store.  Instance sizes may be odd: the
+// thread whose pair ends an odd instance takes its one node alone.
+template <int LAT, int S, typename T>
+__global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k_batch_step_pair(BatchParams<T> p)
+{
+    using L = Lattice<LAT>;
+    using V = typename Pair<T>::type;
+    constexpr int Q = L::Q;
+    static_assert(L::K0 == 1, "the batched pair kernel loads the rest populations as a pair");
+    const uint32_t blk = p.block_begin + blockIdx.x;
+    const uint32_t id = p.blk_inst[blk];
+    const BatchInst d = p.inst[id];
+    const uint32_t local0 = (blk - d.block0) * kBlock + 2 * threadIdx.x;
+    uint32_t* clk = p.clock + 2 * id;
+    const uint32_t step = clk[p.parity];
+    if (blk == d.block0 && threadIdx.x == 0) clk[1 - p.parity] = step + 1;
+    if (local0 >= d.g.cells) return;
+    const bool both = local0 + 1 < d.g.cells;
+    Geom plane = d.g;
+    plane.cells = p.total_nodes;  // the gather's plane stride
+    const uint32_t c0 = d.base + local0;
+    const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
+    const uint32_t hk = mix32(step * 0x9e3779b9u);
+    T f[2][S][Q];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.total_nodes + c0);
+        f[0][s][0] = r.x;
+        f[1][s][0] = r.y;
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (j == 1 && !both) break;
+        const uint32_t local = local0 + j;
+        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
+        pull<LAT, S, T, true>(p.fin, plane, c0 + j, h, f[j], static_cast<const T*>(nullptr));
+        T xi[S + 1];
+        mole_fractions<LAT, S, T>(f[j], xi);
+        T L1[S][S], L2[S][S];
+        relaxation_matrices<S, T>(xi, iv, T(1.0 / L::cs2()), p.relax, L1, L2);
+        collide<LAT, S, T>(f[j], xi, L1, L2, hk ^ (local * 0x27d4eb2du));
+    }
+    if (both) {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                V v;
+                v.x = f[0][s][k];
+                v.y = f[1][s][k];
+                *reinterpret_cast<V*>(p.fout + (size_t)(s * Q + k) * p.total_nodes + c0) = v;
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + c0] = f[0][s][k];
+    }
+}
+
 template <int LAT, int S, typename T>
 __global__ void __launch_bounds__(kBlock) k_batch_mass(BatchParams<T> p)
 {
@@ -245,7 +307,12 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
     const uint32_t blocks = a.block_end - a.block_begin;
     if (blocks == 0) return cudaSuccess;
     switch (op) {
-        case BOP_STEP: k_batch_step<LAT, S, T, false><<<blocks, kBlock, 0, a.stream>>>(p); break;
+        case BOP_STEP:
+            if constexpr (pair_kernel_lattice<LAT, S, T>())
+                k_batch_step_pair<LAT, S, T><<<blocks, kBlock / 2, 0, a.stream>>>(p);
+            else
+                k_batch_step<LAT, S, T, false><<<blocks, kBlock, 0, a.stream>>>(p);
+            break;
         case BOP_STEP_MASS: k_batch_step<LAT, S, T, true><<<blocks, kBlock, 0, a.stream>>>(p); break;
         case BOP_INIT: k_batch_init<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p); break;
         case BOP_MOMENTS: k_batch_moments<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p); break;

@@ -228,6 +228,84 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
     if (MASS) write_mass_partials<S>(xi, active, p.mass);
 }
 
+// Two nodes per thread (c, c + 1 with c even), for the light lattices whose
+// per-node instruction count rather than HBM bandwidth limits the one-node
+// kernel: the pair's rest populations (if the lattice has a rest velocity) come
+// in one 8-byte load and every post-collision plane goes out in one 8-byte
+// store, and the per-thread
+// set-up is shared; the per-node arithmetic is that of k_step, so the results
+// are the same bit for bit.  Blocks of kBlock / 2 threads cover kBlock nodes, the
+// partition of k_step.  Needs an even node count (so that every population plane
+// starts at an even node); no mass partials, no cut faces.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
+template <int LAT, int S, typename T>
+struct PairOccupancy {
+    static constexpr int value = S <= 1 ? 12 : 8;  // blocks of kBlock / 2 threads per SM
+};
+
+template <int LAT, int S, typename T>
+__global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k_step_pair(StepParams<T> p)
+{
+    using L = Lattice<LAT>;
+    using V = typename Pair<T>::type;
+    constexpr int Q = L::Q;
+    constexpr bool REST = L::K0 == 1;  // lattices without a rest velocity gather every population
+    await_previous_grid();
+    const uint32_t c0 = blockIdx.x * kBlock + 2 * threadIdx.x;
+    const uint32_t step = *p.clock_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.clock_out = step + 1;
+    if (c0 >= p.g.cells) return;  // cells is even: both nodes or neither
+    T f[2][S][Q];
+    if constexpr (REST) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.g.cells + c0);
+            f[0][s][0] = r.x;
+            f[1][s][0] = r.y;
+        }
+    }
+    const uint32_t hk = mix32(step * 0x9e3779b9u);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const uint32_t cell = c0 + j;
+        const Neighbourhood h = neighbourhood<L::DIM, false>(p.g, cell);
+        pull<LAT, S, T, REST>(p.fin, p.g, cell, h, f[j], p.xb);
+        T xi[S + 1];
+        mole_fractions<LAT, S, T>(f[j], xi);
+        T L1[S][S], L2[S][S];
+        T xl[S + 1];
+        lambda_composition<S, T>(xi, p.co, p.relax, xl);
+        relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
+        collide<LAT, S, T>(f[j], xi, L1, L2, hk ^ (cell * 0x27d4eb2du));
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            V v;
+            v.x = f[0][s][k];
+            v.y = f[1][s][k];
+            *reinterpret_cast<V*>(p.fout + (size_t)(s * Q + k) * p.g.cells + c0) = v;
+        }
+}
+
+// Whether the pair kernel takes a step of this solver (see k_step_pair).
+template <int LAT, int S, typename T>
+constexpr bool pair_kernel_lattice()
+{
+    return Lattice<LAT>::Q <= 5 && S <= 2 && sizeof(T) == 4;
+}
+
 // Mass partials of the current (post-collision) state without stepping.
 template <int LAT, int S, typename T>
 __global__ void __launch_bounds__(kBlock) k_mass(StepParams<T> p)
@@ -437,6 +515,10 @@ cudaError_t launch(Op op, const KArgs& a)
                 return launch_chained(k_step<LAT, S, T, true, true>, blocks, tb, a.stream, p);
             return cudaErrorInvalidValue;
         } else {
+            if constexpr (pair_kernel_lattice<LAT, S, T>()) {
+                if (op == OP_STEP && tb == kBlock && (a.cells & 1u) == 0)
+                    return launch_chained(k_step_pair<LAT, S, T>, blocks, kBlock / 2, a.stream, p);
+            }
             if (op == OP_STEP) return launch_chained(k_step<LAT, S, T, false, false>, blocks, tb, a.stream, p);
             if (op == OP_STEP_MASS) return launch_chained(k_step<LAT, S, T, true, false>, blocks, tb, a.stream, p);
             k_mass<LAT, S, T><<<blocks, tb, 0, a.stream>>>(p);

@@ -370,7 +370,9 @@ __device__ __forceinline__ int link_wall(int k, const Neighbourhood& h)
 // 2 w_k xi_{s,b} (half-way anti-bounce-back, Sec. 4).  xb holds the evolved
 // species' compositions of the six faces, [6][S]; it is read only on nodes
 // next to a Dirichlet face.
-template <int LAT, int S, typename T>
+// SKIP_REST: the caller has loaded the rest population (k = 0 of a lattice with
+// a rest velocity, which never moves) itself.
+template <int LAT, int S, typename T, bool SKIP_REST = false>
 __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, uint32_t cell,
                                      const Neighbourhood& h, T (&f)[S][Lattice<LAT>::Q],
                                      const T* __restrict__ xb, const Halo<T>* halo = nullptr)
@@ -378,8 +380,9 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
+    static_assert(!SKIP_REST || L::K0 == 1, "only a rest population can be skipped");
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
+    for (int k = SKIP_REST ? 1 : 0; k < Q; ++k) {
         const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
         int32_t off = 0;
         bool bounce = false;
