@@ -329,26 +329,42 @@ struct LamIO<double> {
 // is between distant nodes and between steps, which the float-pair slot
 // carries), so the warp's own sum is a plain FP32 sum.  FP64 solvers keep a
 // double.
-__device__ __forceinline__ void warp_accumulate(float v, double* slot)
+// The slot's old value is read at the start of the step (slot_load), together
+// with the step's other loads, so that the update at its end waits for no load.
+template <typename T>
+struct SlotIO;
+template <>
+struct SlotIO<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 load(const double* slot)
+    {
+        return *reinterpret_cast<const float2*>(slot);
+    }
+};
+template <>
+struct SlotIO<double> {
+    using type = double;
+    static __device__ __forceinline__ double load(const double* slot) { return *slot; }
+};
+
+__device__ __forceinline__ void warp_accumulate(float v, float2 a, double* slot)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if ((threadIdx.x & 31) == 0) {
-        float2* acc = reinterpret_cast<float2*>(slot);
-        const float2 a = *acc;
         float s, e;
         two_sum(a.x, v, s, e);
         e += a.y;
         const float hi = s + e;  // |e| is below an ulp of s: renormalise
-        *acc = make_float2(hi, e - (hi - s));
+        *reinterpret_cast<float2*>(slot) = make_float2(hi, e - (hi - s));
     }
 }
 
-__device__ __forceinline__ void warp_accumulate(double v, double* slot)
+__device__ __forceinline__ void warp_accumulate(double v, double a, double* slot)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) *slot += v;
+    if ((threadIdx.x & 31) == 0) *slot = a + v;
 }
 
 template <typename T>
@@ -386,6 +402,12 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
     Neighbourhood h;
     if (active) h = neighbourhood<Lattice<LAT>::DIM, false>(p.g, cell);
     await_previous_grid();
+    // the warp's accumulator slots (only this warp touches them during the
+    // step) are read by lane 0 right after the step's other loads are issued and
+    // parked in shared memory, so that their update at the end waits for no load
+    const uint32_t warp = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    double* slot = p.gacc + (size_t)warp * NP;
+    __shared__ typename SlotIO<T>::type old_slot[kBlock / 32][NP];
     T dc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) dc[q] = T(0);
@@ -402,6 +424,10 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
                 acc += T(L::w(k)) * hi[k];
             }
             lbar[s] = acc;
+            if (s == 0 && (threadIdx.x & 31) == 0) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) old_slot[threadIdx.x >> 5][q] = SlotIO<T>::load(slot + q);
+            }
 #pragma unroll
             for (int k = 0; k < Q; ++k) d[s][k] = (hi[k] - acc) + lo[k];
         }
@@ -425,12 +451,15 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
             IO::store(p.lam_out, (size_t)s * Q * p.g.cells + plane + dst, lbar[s], mu, neg);
         };
         adjoint_node<LAT, S, T>(f, d, p.co.invD, T(1.0 / L::cs2()), p.relax, dc, emit);
+    } else if ((threadIdx.x & 31) == 0) {  // a warp past the last node
+#pragma unroll
+        for (int q = 0; q < NP; ++q) old_slot[threadIdx.x >> 5][q] = SlotIO<T>::load(slot + q);
     }
     // warp sums of dL/dc (the contributions of different nodes and steps cancel
-    // strongly), accumulated over steps in FP64 in the warp's own slot
-    const uint32_t warp = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    // strongly), accumulated over steps in the warp's own slot
+    __syncwarp();
 #pragma unroll
-    for (int q = 0; q < NP; ++q) warp_accumulate(dc[q], p.gacc + (size_t)warp * NP + q);
+    for (int q = 0; q < NP; ++q) warp_accumulate(dc[q], old_slot[threadIdx.x >> 5][q], slot + q);
 }
 
 template <typename T>

@@ -299,6 +299,10 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k
         }
 }
 
+// Smallest grid stepped by the pair kernel: 2^21 nodes, whose populations
+// (at least 2 x 2 x 3 x 4 B per node) no longer fit the 129 MB L2.
+constexpr uint32_t kPairMinCells = 1u << 21;
+
 // Whether the pair kernel takes a step of this solver (see k_step_pair).
 template <int LAT, int S, typename T>
 constexpr bool pair_kernel_lattice()
@@ -516,7 +520,9 @@ cudaError_t launch(Op op, const KArgs& a)
             return cudaErrorInvalidValue;
         } else {
             if constexpr (pair_kernel_lattice<LAT, S, T>()) {
-                if (op == OP_STEP && tb == kBlock && (a.cells & 1u) == 0)
+                // grids whose state stays in L2 keep one node per thread (more
+                // threads for the latency-bound small grid)
+                if (op == OP_STEP && a.cells >= kPairMinCells && (a.cells & 1u) == 0)
                     return launch_chained(k_step_pair<LAT, S, T>, blocks, kBlock / 2, a.stream, p);
             }
             if (op == OP_STEP) return launch_chained(k_step<LAT, S, T, false, false>, blocks, tb, a.stream, p);
