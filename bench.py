@@ -656,8 +656,8 @@ def measure_batch(steps: int, warmup: int, local: int, count: int = BATCH_COUNT,
     nodes = float(sum(int(g[0]) * int(g[1]) for g in grids))
     bytes_per_step = 2.0 * 2 * 5 * 4 * nodes
     roof = hbm_roofline(bytes_per_step, ms / steps,
-                        recorded_traffic("traffic_batch_d2q5_4096_f32.json", [count]) if chosen == 0
-                        else None)
+                        recorded_traffic("traffic_batch_d2q5_4096_f32.json", [count, int(chosen)])
+                        if chosen % 7 == 0 else None)
     roof["note"] = "algorithmic bytes of a streamed step; L2-blocked schedules move less"
     out = {
         "value": round(count * steps / BATCH_SOLVE_STEPS / (ms * 1e-3), 3),
@@ -672,7 +672,9 @@ def measure_batch(steps: int, warmup: int, local: int, count: int = BATCH_COUNT,
             "workload": "batched: %d ternary D2Q5 FP32 solves of %d steps, sides uniform in "
                         "[32, 256] (%.1f M nodes), D_ij uniform in [0.01, 0.12], sine/periodic "
                         "and tanh/no-flux-x fields" % (count, BATCH_SOLVE_STEPS, nodes / 1e6),
-            "schedule": int(chosen),
+            "candidate": int(chosen),
+            "schedule": int(chosen) % 7,
+            "nodes_per_thread": 1 + int(chosen) // 7,
             "tuner_ms_per_step": [round(float(v), 4) for v in tune_ms],
             "l2": "state %.1f GB per step vs 129 MB L2" % (bytes_per_step / 1e9),
         },
@@ -1053,7 +1055,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the headline workload (not the other parts of the metric)")
     ap.add_argument("--batch-schedule", type=int, default=-1,
-                    help="batched workload: fixed step schedule (0..6) instead of the tuner's")
+                    help="batched workload: fixed step candidate (0..13: schedule + 7 x kernel "
+                         "shape) instead of the tuner's")
     ap.add_argument("--grid", type=int, default=256,
                     help="grid edge (256 selects each workload's own size)")
     args = ap.parse_args()

@@ -408,8 +408,9 @@ int lbms_slab_step(lbms_t* const* subs, int count, long n_steps);
 
 typedef struct lbms_batch_s lbms_batch_t;
 
-/* Number of step schedules lbms_batch_tune chooses from. */
-#define LBMS_BATCH_CANDIDATES 7
+/* Number of step candidates lbms_batch_tune chooses from: 7 schedules x 2
+ * kernel shapes. */
+#define LBMS_BATCH_CANDIDATES 14
 
 /*
  * Workspace bytes for `count` instances with grids[3 * i + {0,1,2}] = {nx, ny,
@@ -444,9 +445,10 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
 int lbms_batch_set_state(lbms_batch_t* b, const void* x0, const int64_t* offsets);
 
 /*
- * Advance every instance by n_steps (Eqs. 3-13a/3-13b), with the schedule
- * chosen by lbms_batch_tune or lbms_batch_set_schedule (default: 0, all
- * instances per launch).  Each instance evolves exactly as lbms_step would
+ * Advance every instance by n_steps (Eqs. 3-13a/3-13b), with the candidate
+ * (schedule and kernel shape) chosen by lbms_batch_tune or
+ * lbms_batch_set_schedule (default: all instances per launch, see below).
+ * Each instance evolves exactly as lbms_step would
  * evolve it alone, bit for bit.  The last step writes the mass partials.
  */
 int lbms_batch_step(lbms_batch_t* b, long n_steps);
@@ -467,11 +469,17 @@ int lbms_batch_mass(lbms_batch_t* b, double* mass_out);
 int lbms_batch_status(lbms_batch_t* b, uint32_t* flags);
 
 /*
- * Step schedules: 0 streams all instances through HBM every step (CUDA graph
- * of 32 steps); 1..6 run groups of consecutive instances whose two population
- * buffers fit in 24, 24, 48, 48, 96, 96 MB for 8 or 32 steps each (chunk
- * 8, 32, 8, 32, 8, 32), so that a group stays in L2 between its steps.
- * Results do not depend on the schedule.
+ * Step candidates c = schedule + 7 * shape.  Schedules (c % 7): 0 streams all
+ * instances through HBM every step (CUDA graph of 32 steps); 1..6 run groups
+ * of consecutive instances whose two population buffers fit in 24, 24, 48,
+ * 48, 96, 96 MB for 8 or 32 steps each (chunk 8, 32, 8, 32, 8, 32), so that a
+ * group stays in L2 between its steps.  Kernel shapes (c / 7): 0 takes one
+ * node per thread (blocks of 256 threads), 1 two nodes per thread (blocks of
+ * 128 threads over the same 256-node blocks; paired loads of the rest
+ * populations and paired stores), available for D2Q5 with n <= 3 in F32 only
+ * (LBMS_EINVAL otherwise).  The default is candidate 7 where shape 1 exists,
+ * else 0.  Results do not depend on the candidate.  lbms_batch_get_schedule
+ * returns the current candidate.
  */
 int lbms_batch_set_schedule(lbms_batch_t* b, int candidate);
 int lbms_batch_get_schedule(const lbms_batch_t* b);
@@ -483,11 +491,12 @@ int lbms_batch_get_schedule(const lbms_batch_t* b);
 int lbms_batch_launches_per_step(const lbms_batch_t* b);
 
 /*
- * Schedule tuner: times every candidate over trial_steps steps (after one
+ * Candidate tuner: times every candidate over trial_steps steps (after one
  * untimed warm-up of the same length), keeps the fastest and returns it in
- * *chosen; ms_per_step, if not NULL, receives LBMS_BATCH_CANDIDATES timings.
- * It advances the instances by 2 * LBMS_BATCH_CANDIDATES * trial_steps steps:
- * call it before lbms_batch_set_state.
+ * *chosen; ms_per_step, if not NULL, receives LBMS_BATCH_CANDIDATES timings
+ * (-1 for the candidates this batch cannot run).
+ * It advances the instances by up to 2 * LBMS_BATCH_CANDIDATES * trial_steps
+ * steps: call it before lbms_batch_set_state.
  */
 int lbms_batch_tune(lbms_batch_t* b, int trial_steps, double* ms_per_step, int* chosen);
 

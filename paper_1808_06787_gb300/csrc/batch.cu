@@ -28,7 +28,12 @@ struct Candidate {
     size_t budget;
     int chunk;
 };
-constexpr Candidate kCandidates[LBMS_BATCH_CANDIDATES] = {
+// Candidates of the tuner: schedule c % kSchedules with the kernel shape
+// c / kSchedules (0: one node per thread; 1: two nodes per thread, for the
+// lattices, species counts and dtypes that have the pair kernel).
+constexpr int kSchedules = 7;
+static_assert(LBMS_BATCH_CANDIDATES == 2 * kSchedules, "candidates: schedules x kernel shapes");
+constexpr Candidate kCandidates[kSchedules] = {
     {0, 0},
     {size_t(24) << 20, 8},  {size_t(24) << 20, 32},
     {size_t(48) << 20, 8},  {size_t(48) << 20, 32},
@@ -144,6 +149,7 @@ struct lbms_batch_s {
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
     int schedule = 0;
+    int shape = 0;  // nodes per thread of the plain steps - 1
     std::vector<std::pair<uint32_t, uint32_t>> groups;  // block ranges of the grouped schedule
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long steps = 0;
@@ -204,6 +210,7 @@ cudaError_t bstep(const lbms_batch_t* b, int src, bool mass, uint32_t b0, uint32
     a.fin = b->f[src];
     a.fout = b->f[1 - src];
     a.parity = src;
+    a.nodes_per_thread = b->shape + 1;
     return bdispatch(b, mass ? BOP_STEP_MASS : BOP_STEP, a);
 }
 
@@ -244,6 +251,13 @@ void drop_graphs(lbms_batch_t* b)
             cudaGraphExecDestroy(b->graph[i]);
             b->graph[i] = nullptr;
         }
+}
+
+// Whether the batch's steps have a two-nodes-per-thread kernel (ternary or
+// binary D2Q5 in FP32: the lattices with Q <= 5 among the batched ones).
+bool has_pair_shape(const lbms_batch_t* b)
+{
+    return b->lattice == LBMS_D2Q5 && b->S <= 2 && b->dtype == LBMS_F32;
 }
 
 // Steps one graph holds: kStreamSteps for the streamed schedule, one chunk of
@@ -361,6 +375,7 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
     b->relax = relax;
     b->count = count;
     b->es = dtype == LBMS_F64 ? 8 : 4;
+    b->shape = has_pair_shape(b) ? 1 : 0;  // the faster shape where it exists
     b->lay = L;
     b->ws = static_cast<char*>(workspace);
     b->f[0] = b->ws;
@@ -637,16 +652,21 @@ int lbms_batch_set_schedule(lbms_batch_t* b, int candidate)
     if (!b) return LBMS_EINVAL;
     if (candidate < 0 || candidate >= LBMS_BATCH_CANDIDATES)
         return bfail(b, LBMS_EINVAL, "schedule %d is not one of 0..%d", candidate, LBMS_BATCH_CANDIDATES - 1);
-    if (candidate == b->schedule) return LBMS_OK;
+    const int schedule = candidate % kSchedules, shape = candidate / kSchedules;
+    if (shape == 1 && !has_pair_shape(b))
+        return bfail(b, LBMS_EINVAL, "candidate %d needs the two-nodes-per-thread kernel (D2Q5, n <= 3, F32)",
+                     candidate);
+    if (schedule == b->schedule && shape == b->shape) return LBMS_OK;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "cudaStreamSynchronize");
     drop_graphs(b);
-    b->schedule = candidate;
-    if (candidate > 0) build_groups(b, kCandidates[candidate].budget);
+    b->schedule = schedule;
+    b->shape = shape;
+    if (schedule > 0) build_groups(b, kCandidates[schedule].budget);
     return LBMS_OK;
 }
 
-int lbms_batch_get_schedule(const lbms_batch_t* b) { return b ? b->schedule : -1; }
+int lbms_batch_get_schedule(const lbms_batch_t* b) { return b ? b->schedule + kSchedules * b->shape : -1; }
 
 int lbms_batch_launches_per_step(const lbms_batch_t* b)
 {
@@ -666,6 +686,10 @@ int lbms_batch_tune(lbms_batch_t* b, int trial_steps, double* ms_per_step, int* 
     if (e != cudaSuccess) return bcuda(b, e, "cudaEventCreate");
     int rc = LBMS_OK;
     for (int c = 0; c < LBMS_BATCH_CANDIDATES && rc == LBMS_OK; ++c) {
+        if (c / kSchedules == 1 && !has_pair_shape(b)) {
+            if (ms_per_step) ms_per_step[c] = -1.0;  // not available for this batch
+            continue;
+        }
         rc = lbms_batch_set_schedule(b, c);
         if (rc == LBMS_OK) rc = lbms_batch_step(b, trial_steps);  // warm-up, builds the graphs
         if (rc != LBMS_OK) break;

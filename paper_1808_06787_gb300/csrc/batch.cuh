@@ -44,6 +44,7 @@ struct BArgs {
     void* field_x = nullptr;                  // moments: mole fractions
     void* field_J = nullptr;                  // moments: fluxes or null
     const long long* field_off = nullptr;     // [count] element offset of instance i's x block
+    int nodes_per_thread = 1;                 // plain steps: 1 or 2 (k_batch_step_pair)
     cudaStream_t stream = nullptr;
 };
 
@@ -308,10 +309,13 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
     if (blocks == 0) return cudaSuccess;
     switch (op) {
         case BOP_STEP:
-            if constexpr (pair_kernel_lattice<LAT, S, T>())
-                k_batch_step_pair<LAT, S, T><<<blocks, kBlock / 2, 0, a.stream>>>(p);
-            else
-                k_batch_step<LAT, S, T, false><<<blocks, kBlock, 0, a.stream>>>(p);
+            if constexpr (pair_kernel_lattice<LAT, S, T>()) {
+                if (a.nodes_per_thread == 2) {
+                    k_batch_step_pair<LAT, S, T><<<blocks, kBlock / 2, 0, a.stream>>>(p);
+                    break;
+                }
+            }
+            k_batch_step<LAT, S, T, false><<<blocks, kBlock, 0, a.stream>>>(p);
             break;
         case BOP_STEP_MASS: k_batch_step<LAT, S, T, true><<<blocks, kBlock, 0, a.stream>>>(p); break;
         case BOP_INIT: k_batch_init<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p); break;

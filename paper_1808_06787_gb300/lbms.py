@@ -52,7 +52,7 @@ EXPORTED = (
     "lbms_adjoint_step", "lbms_adjoint_steps", "lbms_adjoint_initial", "lbms_adjoint_reduce",
     "lbms_set_subdomain", "lbms_halo_buffers", "lbms_slab_step",
 )
-BATCH_CANDIDATES = 7
+BATCH_CANDIDATES = 14
 
 _lock = threading.Lock()
 _lib = None
@@ -648,8 +648,9 @@ class BatchSolver:
         return int(load().lbms_batch_launches_per_step(self._h))
 
     def tune(self, trial_steps: int = 32):
-        """Time every step schedule and keep the fastest (advances the state: call
-        before set_state).  Returns (chosen, ms_per_step of each candidate)."""
+        """Time every step candidate (schedule x kernel shape) and keep the fastest
+        (advances the state: call before set_state).  Returns (chosen, ms_per_step
+        of each candidate; -1 for the candidates this batch cannot run)."""
         times = np.zeros(BATCH_CANDIDATES, dtype=np.float64)
         chosen = ctypes.c_int()
         _bcheck(self._h, load().lbms_batch_tune(self._h, int(trial_steps), times.ctypes.data_as(ctypes.c_void_p),

@@ -85,9 +85,19 @@ def test_every_schedule_gives_the_same_result(dtype):
         bcs.append((P,) * 6)
         x0s.append(sy.sin_modes(3, L, L, amp=0.05, seed=900 + i))
     ref = None
-    for cand in range(7):
+    # every schedule with both kernel shapes (the two-nodes-per-thread shape
+    # exists for FP32 only)
+    from paper_1808_06787_gb300 import LbmsError
+
+    for cand in range(14):
         b = BatchSolver("D2Q5", Ds, grids, bcs=bcs, dtype=dtype)
+        if cand >= 7 and dtype == torch.float64:
+            with pytest.raises(LbmsError, match="two-nodes-per-thread"):
+                b.set_schedule(cand)
+            b.close()
+            continue
         b.set_schedule(cand)
+        assert b.schedule == cand
         b.set_state([torch.from_numpy(x) for x in x0s])
         b.step(71)
         x = b.moments()
@@ -138,8 +148,12 @@ def test_tuner_picks_a_valid_schedule():
     grids, Ds, bcs = sy.batch_instances(64, seed=8)
     b = BatchSolver("D2Q5", Ds, grids, bcs=bcs)
     chosen, times = b.tune(trial_steps=8)
-    assert 0 <= chosen < 7 and b.schedule == chosen
+    assert 0 <= chosen < 14 and b.schedule == chosen
     assert np.all(times > 0) and times[chosen] == times.min()
+    # a batch without the two-nodes-per-thread kernel reports those candidates as -1
+    b64 = BatchSolver("D2Q5", Ds, grids, bcs=bcs, dtype=torch.float64)
+    chosen, times = b64.tune(trial_steps=4)
+    assert 0 <= chosen < 7 and np.all(times[7:] == -1.0) and np.all(times[:7] > 0)
 
 
 def test_batch_4096_uneven_d2q5_instances_full_size():
