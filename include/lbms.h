@@ -48,8 +48,8 @@ typedef struct lbms_s lbms_t;
 
 /* Lattices of Sec. 3.1: D2Q5 (Eq. 3-7), D2Q9 (Eq. 3-8), D3Q7 (Eq. 3-10),
  * D3Q15 (Eq. 3-11), D1Q3 (Eq. 3-5), and the two without a rest velocity, D2Q4
- * (Eq. 3-6) and D3Q6 (Eq. 3-9).  Batched solves take the first three; the
- * adjoint entry points all but D2Q4 and D3Q6. */
+ * (Eq. 3-6) and D3Q6 (Eq. 3-9).  Batched solves and the adjoint entry points
+ * take all seven. */
 enum {
     LBMS_D2Q5 = 0,
     LBMS_D2Q9 = 1,
@@ -428,8 +428,10 @@ size_t lbms_batch_workspace_size(int lattice, int n_species, int count, const in
  *   grids  host array of count * 3 extents.
  *   D      host array of count * n * n diffusivities (instance-major), each
  *          block symmetric with positive off-diagonal entries.
- *   bc     host array of count * 6 face kinds as for lbms_create, or NULL for
- *          all periodic.
+ *   bc     host array of count * 6 face kinds as for lbms_create (periodic,
+ *          no-flux or Dirichlet; Dirichlet faces need
+ *          lbms_batch_set_boundary before the first step), or NULL for all
+ *          periodic.
  * Errors as for lbms_create (messages via lbms_batch_last_error(NULL)).
  */
 int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count, const int* grids,
@@ -461,6 +463,14 @@ int lbms_batch_step(lbms_batch_t* b, long n_steps);
  */
 int lbms_batch_moments(lbms_batch_t* b, void* x_sigma, void* J_sigma, const int64_t* offsets);
 
+/*
+ * Composition xi_b (host array of all n mole fractions) held on Dirichlet face
+ * `face` (0..5) of instance `instance`, as lbms_set_boundary for a single
+ * solve: stream-ordered, synchronises the stream; LBMS_EINVAL for a face that
+ * is not Dirichlet or a bad composition.
+ */
+int lbms_batch_set_boundary(lbms_batch_t* b, int instance, int face, const double* xi_b);
+
 /* Per-instance species totals, mass_out[i * n + s], as lbms_mass.  Host array;
  * synchronises the stream. */
 int lbms_batch_mass(lbms_batch_t* b, double* mass_out);
@@ -476,7 +486,8 @@ int lbms_batch_status(lbms_batch_t* b, uint32_t* flags);
  * group stays in L2 between its steps.  Kernel shapes (c / 7): 0 takes one
  * node per thread (blocks of 256 threads), 1 two nodes per thread (blocks of
  * 128 threads over the same 256-node blocks; paired loads of the rest
- * populations and paired stores), available for D2Q5 with n <= 3 in F32 only
+ * populations and paired stores), available for D2Q5, D1Q3 and D2Q4 with
+ * n <= 3 in F32 only
  * (LBMS_EINVAL otherwise).  The default is candidate 7 where shape 1 exists,
  * else 0.  Results do not depend on the candidate.  lbms_batch_get_schedule
  * returns the current candidate.

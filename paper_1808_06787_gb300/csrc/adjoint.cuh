@@ -136,24 +136,29 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
     // (a) Lambda fixed: nu = Omega^T lambda, mu = lambda - nu + sum_k w_k nu_k
     // (b) accumulators H = <lambda, odd(g)> + <lambda, even(g)> r
     // first pass: H and wnu = sum_k w_k nu_k
+    // (a rest population, k = 0, is the even part of itself; lattices without a
+    // rest velocity, K0 = 0, have pairs only)
+    constexpr bool REST = L::K0 == 1;
     T Ga[S][S], Gs[S][S], wnu[S];
 #pragma unroll
     for (int i = 0; i < S; ++i)
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             Ga[i][j] = T(0);
-            Gs[i][j] = lam[i][0] * (f[j][0] - T(L::w(0)) * xi[j]);
+            Gs[i][j] = REST ? lam[i][0] * (f[j][0] - T(L::w(0)) * xi[j]) : T(0);
         }
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         T nu0 = T(0);
+        if (REST) {
 #pragma unroll
-        for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
-        wnu[j] = T(L::w(0)) * nu0;
+            for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
+        }
+        wnu[j] = REST ? T(L::w(0)) * nu0 : T(0);
     }
 #pragma unroll
     for (int pr = 0; pr < L::NPAIR; ++pr) {
-        const int ka = 2 * pr + 1, kb = 2 * pr + 2;
+        const int ka = L::K0 + 2 * pr, kb = ka + 1;
         const T wp = T(L::w(ka));
         T ls[S], la[S], gs[S], ga[S];
 #pragma unroll
@@ -230,16 +235,18 @@ __device__ __forceinline__ void adjoint_node(const T (&f)[S][Lattice<LAT>::Q],
     }
     // second pass: mu = lambda - nu + add, nu of the rest population and of the
     // odd (Lambda_1) and even (Lambda_2) parts of every pair
+    if constexpr (REST) {
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-        T nu0 = T(0);
+        for (int j = 0; j < S; ++j) {
+            T nu0 = T(0);
 #pragma unroll
-        for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
-        emit(j, 0, lam[j][0] - nu0 + add[j]);
+            for (int i = 0; i < S; ++i) nu0 += L2[i][j] * lam[i][0];
+            emit(j, 0, lam[j][0] - nu0 + add[j]);
+        }
     }
 #pragma unroll
     for (int pr = 0; pr < L::NPAIR; ++pr) {
-        const int ka = 2 * pr + 1, kb = 2 * pr + 2;
+        const int ka = L::K0 + 2 * pr, kb = ka + 1;
         T ls[S], la[S];
 #pragma unroll
         for (int i = 0; i < S; ++i) {
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(kBlock, AdjOccupancy<LAT, S, T>::value) k_adjo
             const uint32_t dst = bounce ? cell : (uint32_t)((int32_t)cell + off);
             const size_t plane = (size_t)(bounce ? opp<LAT>(k) : k) * p.g.cells;
             bool neg = false;
-            if (k != 0 && h.dir) {
+            if (k >= L::K0 && h.dir) {
                 const int wf = link_wall<LAT>(k, h);
                 neg = wf >= 0 && ((h.dir >> wf) & 1u);
             }
@@ -570,5 +577,7 @@ cudaError_t adj_dispatch_d2q9(AdjOp op, int dtype, const AArgs& a);
 cudaError_t adj_dispatch_d3q7(AdjOp op, int dtype, const AArgs& a);
 cudaError_t adj_dispatch_d3q15(AdjOp op, int dtype, const AArgs& a);
 cudaError_t adj_dispatch_d1q3(AdjOp op, int dtype, const AArgs& a);
+cudaError_t adj_dispatch_d2q4(AdjOp op, int dtype, const AArgs& a);
+cudaError_t adj_dispatch_d3q6(AdjOp op, int dtype, const AArgs& a);
 
 }  // namespace lbms

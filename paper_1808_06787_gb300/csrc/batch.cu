@@ -41,13 +41,28 @@ constexpr Candidate kCandidates[kSchedules] = {
 };
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-int lattice_q(int lat) { return lat == LBMS_D2Q5 ? 5 : lat == LBMS_D2Q9 ? 9 : lat == LBMS_D3Q7 ? 7 : 0; }
-int lattice_dim(int lat) { return lat == LBMS_D3Q7 ? 3 : 2; }
+int lattice_q(int lat)
+{
+    switch (lat) {
+        case LBMS_D2Q5: return 5;
+        case LBMS_D2Q9: return 9;
+        case LBMS_D3Q7: return 7;
+        case LBMS_D3Q15: return 15;
+        case LBMS_D1Q3: return 3;
+        case LBMS_D2Q4: return 4;
+        case LBMS_D3Q6: return 6;
+        default: return 0;
+    }
+}
+int lattice_dim(int lat)
+{
+    return lat == LBMS_D3Q7 || lat == LBMS_D3Q15 || lat == LBMS_D3Q6 ? 3 : (lat == LBMS_D1Q3 ? 1 : 2);
+}
 
 struct BLayout {
     uint32_t total_blocks = 0, total_nodes = 0;
     size_t f_bytes = 0, off_f1 = 0, off_partials = 0, off_mass = 0, off_inst = 0, off_blk = 0,
-           off_invD = 0, off_clock = 0, off_foff = 0, off_status = 0, off_staging = 0,
+           off_invD = 0, off_clock = 0, off_foff = 0, off_xb = 0, off_status = 0, off_staging = 0,
            staging_bytes = 0, total = 0;
 };
 
@@ -61,7 +76,8 @@ bool batch_layout(int lat, int n, int count, const int* grids, int dtype, BLayou
     for (int i = 0; i < count; ++i) {
         const int* g = grids + 3 * i;
         if (g[0] < 1 || g[1] < 1 || g[2] < 1) return false;
-        if (dim == 2 && g[2] != 1) return false;
+        if (dim < 3 && g[2] != 1) return false;
+        if (dim == 1 && g[1] != 1) return false;
         const double c = (double)g[0] * g[1] * g[2];
         if (c > (double)LBMS_MAX_CELLS) return false;
         blocks += ceil(c / kBlock);
@@ -80,7 +96,9 @@ bool batch_layout(int lat, int n, int count, const int* grids, int dtype, BLayou
     L->off_invD = L->off_blk + align_up((size_t)L->total_blocks * sizeof(uint32_t));
     L->off_clock = L->off_invD + align_up((size_t)count * n * n * es);
     L->off_foff = L->off_clock + align_up((size_t)count * 2 * sizeof(uint32_t));
-    L->off_status = L->off_foff + align_up((size_t)count * sizeof(long long));
+    L->off_xb = L->off_foff + align_up((size_t)count * sizeof(long long));
+    // Dirichlet compositions [count][6][S]
+    L->off_status = L->off_xb + align_up((size_t)count * 6 * (n - 1) * es);
     L->off_staging = L->off_status + kAlign;
     // staging: large enough for the biggest instance's fields, at most 16 MiB beyond that
     const size_t biggest = (size_t)max_field * n * (1 + dim) * es;
@@ -143,6 +161,9 @@ struct lbms_batch_s {
     void* invD_dev = nullptr;
     uint32_t* clock = nullptr;
     long long* foff_dev = nullptr;
+    void* xb_dev = nullptr;               // [count][6][S] Dirichlet compositions, solver dtype
+    std::vector<uint32_t> dirichlet;      // per instance: Dirichlet face mask
+    std::vector<uint32_t> xb_set;         // per instance: Dirichlet faces whose composition is set
     uint32_t* status = nullptr;
     char* staging = nullptr;
     int fixed_shift = 32;
@@ -179,7 +200,11 @@ cudaError_t bdispatch(const lbms_batch_t* b, BatchOp op, const BArgs& a)
     switch (b->lattice) {
         case LBMS_D2Q5: return batch_dispatch_d2q5(op, b->dtype, a);
         case LBMS_D2Q9: return batch_dispatch_d2q9(op, b->dtype, a);
-        default: return batch_dispatch_d3q7(op, b->dtype, a);
+        case LBMS_D3Q7: return batch_dispatch_d3q7(op, b->dtype, a);
+        case LBMS_D3Q15: return batch_dispatch_d3q15(op, b->dtype, a);
+        case LBMS_D1Q3: return batch_dispatch_d1q3(op, b->dtype, a);
+        case LBMS_D2Q4: return batch_dispatch_d2q4(op, b->dtype, a);
+        default: return batch_dispatch_d3q6(op, b->dtype, a);
     }
 }
 
@@ -199,6 +224,7 @@ BArgs bargs(const lbms_batch_t* b, cudaStream_t st, uint32_t b0, uint32_t b1)
     a.fixed_shift = b->fixed_shift;
     a.status = b->status;
     a.field_off = b->foff_dev;
+    a.xb = b->xb_dev;
     a.stream = st;
     return a;
 }
@@ -254,10 +280,10 @@ void drop_graphs(lbms_batch_t* b)
 }
 
 // Whether the batch's steps have a two-nodes-per-thread kernel (ternary or
-// binary D2Q5 in FP32: the lattices with Q <= 5 among the batched ones).
+// binary FP32 solves on the lattices with Q <= 5: D2Q5, D1Q3, D2Q4).
 bool has_pair_shape(const lbms_batch_t* b)
 {
-    return b->lattice == LBMS_D2Q5 && b->S <= 2 && b->dtype == LBMS_F32;
+    return b->Q <= 5 && b->S <= 2 && b->dtype == LBMS_F32;
 }
 
 // Steps one graph holds: kStreamSteps for the streamed schedule, one chunk of
@@ -359,7 +385,7 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
         if (bc)
             for (int a = 0; a < dim; ++a) {
                 const int lo = bc[6 * c + 2 * a], hi = bc[6 * c + 2 * a + 1];
-                if ((lo != LBMS_PERIODIC && lo != LBMS_NOFLUX) || (hi != LBMS_PERIODIC && hi != LBMS_NOFLUX) ||
+                if (lo < LBMS_PERIODIC || lo > LBMS_DIRICHLET || hi < LBMS_PERIODIC || hi > LBMS_DIRICHLET ||
                     ((lo == LBMS_PERIODIC) != (hi == LBMS_PERIODIC)))
                     return bfail(nullptr, LBMS_EINVAL, "instance %d: invalid or unpaired faces on axis %d", c, a);
             }
@@ -387,6 +413,9 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
     b->invD_dev = b->ws + L.off_invD;
     b->clock = reinterpret_cast<uint32_t*>(b->ws + L.off_clock);
     b->foff_dev = reinterpret_cast<long long*>(b->ws + L.off_foff);
+    b->xb_dev = b->ws + L.off_xb;
+    b->dirichlet.assign(count, 0u);
+    b->xb_set.assign(count, 0u);
     b->status = reinterpret_cast<uint32_t*>(b->ws + L.off_status);
     b->staging = b->ws + L.off_staging;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -402,13 +431,17 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
         KArgs ka;
         ka.nx = grids[3 * c]; ka.ny = grids[3 * c + 1]; ka.nz = grids[3 * c + 2];
         ka.cells = (uint32_t)((size_t)ka.nx * ka.ny * ka.nz);
-        uint32_t nf = 0;
+        uint32_t nf = 0, dr = 0;
         if (bc)
             for (int a = 0; a < dim; ++a) {
                 if (bc[6 * c + 2 * a] == LBMS_NOFLUX) nf |= 1u << (2 * a);
                 if (bc[6 * c + 2 * a + 1] == LBMS_NOFLUX) nf |= 1u << (2 * a + 1);
+                if (bc[6 * c + 2 * a] == LBMS_DIRICHLET) dr |= 1u << (2 * a);
+                if (bc[6 * c + 2 * a + 1] == LBMS_DIRICHLET) dr |= 1u << (2 * a + 1);
             }
         ka.noflux = nf;
+        ka.dirichlet = dr;
+        b->dirichlet[c] = dr;
         BatchInst& d = b->inst[c];
         d.g = make_geom(ka);
         d.base = block * kBlock;
@@ -516,6 +549,10 @@ int lbms_batch_step(lbms_batch_t* b, long n_steps)
 {
     if (!b) return LBMS_EINVAL;
     if (n_steps < 0) return bfail(b, LBMS_EINVAL, "n_steps = %ld is negative", n_steps);
+    for (int c = 0; c < b->count; ++c)
+        if (b->dirichlet[c] & ~b->xb_set[c])
+            return bfail(b, LBMS_EINVAL, "instance %d: Dirichlet face mask 0x%x has no composition set", c,
+                         b->dirichlet[c] & ~b->xb_set[c]);
     b->err[0] = '\0';
     if (n_steps == 0) return LBMS_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -647,6 +684,37 @@ int lbms_batch_status(lbms_batch_t* b, uint32_t* flags)
     return e == cudaSuccess ? LBMS_OK : bcuda(b, e, "status copy");
 }
 
+int lbms_batch_set_boundary(lbms_batch_t* b, int instance, int face, const double* xi_b)
+{
+    if (!b) return LBMS_EINVAL;
+    if (instance < 0 || instance >= b->count) return bfail(b, LBMS_EINVAL, "instance %d out of range", instance);
+    if (face < 0 || face > 5 || !((b->dirichlet[instance] >> face) & 1u))
+        return bfail(b, LBMS_EINVAL, "instance %d: face %d is not a Dirichlet face", instance, face);
+    if (!xi_b) return bfail(b, LBMS_EINVAL, "xi_b is NULL");
+    double sum = 0.0;
+    for (int s = 0; s < b->n; ++s) {
+        if (!isfinite(xi_b[s]) || xi_b[s] < -1e-6 || xi_b[s] > 1.0 + 1e-6)
+            return bfail(b, LBMS_EINVAL, "xi_b[%d] = %g is not a mole fraction", s, xi_b[s]);
+        sum += xi_b[s];
+    }
+    if (fabs(sum - 1.0) > 1e-6) return bfail(b, LBMS_EINVAL, "the composition sums to %.9g, not 1", sum);
+    b->err[0] = '\0';
+    double v64[LBMS_MAX_SPECIES];
+    float v32[LBMS_MAX_SPECIES];
+    for (int s = 0; s < b->S; ++s) {
+        v64[s] = xi_b[s];
+        v32[s] = (float)xi_b[s];
+    }
+    const void* src = b->dtype == LBMS_F64 ? static_cast<const void*>(v64) : static_cast<const void*>(v32);
+    char* dst = static_cast<char*>(b->xb_dev) + ((size_t)instance * 6 + face) * b->S * b->es;
+    cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)b->S * b->es, cudaMemcpyHostToDevice, b->stream);
+    // the copy reads pageable memory: wait for it before the locals go away
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "boundary composition copy");
+    b->xb_set[instance] |= 1u << face;
+    return LBMS_OK;
+}
+
 int lbms_batch_set_schedule(lbms_batch_t* b, int candidate)
 {
     if (!b) return LBMS_EINVAL;
@@ -654,7 +722,7 @@ int lbms_batch_set_schedule(lbms_batch_t* b, int candidate)
         return bfail(b, LBMS_EINVAL, "schedule %d is not one of 0..%d", candidate, LBMS_BATCH_CANDIDATES - 1);
     const int schedule = candidate % kSchedules, shape = candidate / kSchedules;
     if (shape == 1 && !has_pair_shape(b))
-        return bfail(b, LBMS_EINVAL, "candidate %d needs the two-nodes-per-thread kernel (D2Q5, n <= 3, F32)",
+        return bfail(b, LBMS_EINVAL, "candidate %d needs the two-nodes-per-thread kernel (Q <= 5, n <= 3, F32)",
                      candidate);
     if (schedule == b->schedule && shape == b->shape) return LBMS_OK;
     cudaError_t e = cudaStreamSynchronize(b->stream);

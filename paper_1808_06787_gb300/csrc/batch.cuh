@@ -45,6 +45,7 @@ struct BArgs {
     void* field_J = nullptr;                  // moments: fluxes or null
     const long long* field_off = nullptr;     // [count] element offset of instance i's x block
     int nodes_per_thread = 1;                 // plain steps: 1 or 2 (k_batch_step_pair)
+    const void* xb = nullptr;                 // [count][6][S] Dirichlet compositions
     cudaStream_t stream = nullptr;
 };
 
@@ -73,6 +74,7 @@ struct BatchParams {
     T* x_out;
     T* J_out;
     const long long* field_off;
+    const T* __restrict__ xb;  // [count][6][S] Dirichlet compositions
 };
 
 template <int LAT, int S, typename T, bool MASS>
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
         plane.cells = p.total_nodes;  // the gather's plane stride
         const uint32_t cell = d.base + local;
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, plane, cell, h, f, static_cast<const T*>(nullptr));
+        pull<LAT, S, T>(p.fin, plane, cell, h, f, p.xb + (size_t)id * 6 * S);
         mole_fractions<LAT, S, T>(f, xi);
         if (MASS) check_range<S, T>(xi, p.status);  // once per step call
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k
     using L = Lattice<LAT>;
     using V = typename Pair<T>::type;
     constexpr int Q = L::Q;
-    static_assert(L::K0 == 1, "the batched pair kernel loads the rest populations as a pair");
+    constexpr bool REST = L::K0 == 1;  // lattices without a rest velocity gather every population
     const uint32_t blk = p.block_begin + blockIdx.x;
     const uint32_t id = p.blk_inst[blk];
     const BatchInst d = p.inst[id];
@@ -136,18 +138,20 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k
     const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
     const uint32_t hk = mix32(step * 0x9e3779b9u);
     T f[2][S][Q];
+    if constexpr (REST) {
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.total_nodes + c0);
-        f[0][s][0] = r.x;
-        f[1][s][0] = r.y;
+        for (int s = 0; s < S; ++s) {
+            const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.total_nodes + c0);
+            f[0][s][0] = r.x;
+            f[1][s][0] = r.y;
+        }
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         if (j == 1 && !both) break;
         const uint32_t local = local0 + j;
         const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
-        pull<LAT, S, T, true>(p.fin, plane, c0 + j, h, f[j], static_cast<const T*>(nullptr));
+        pull<LAT, S, T, REST>(p.fin, plane, c0 + j, h, f[j], p.xb + (size_t)id * 6 * S);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f[j], xi);
         T L1[S][S], L2[S][S];
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
         Geom plane = d.g;
         plane.cells = p.total_nodes;
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, plane, cell, h, f, static_cast<const T*>(nullptr));
+        pull<LAT, S, T>(p.fin, plane, cell, h, f, p.xb + (size_t)id * 6 * S);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
@@ -305,6 +309,7 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
     p.x_out = static_cast<T*>(a.field_x);
     p.J_out = static_cast<T*>(a.field_J);
     p.field_off = a.field_off;
+    p.xb = static_cast<const T*>(a.xb);
     const uint32_t blocks = a.block_end - a.block_begin;
     if (blocks == 0) return cudaSuccess;
     switch (op) {
@@ -349,5 +354,9 @@ cudaError_t batch_dispatch_lattice(BatchOp op, int dtype, const BArgs& a)
 cudaError_t batch_dispatch_d2q5(BatchOp op, int dtype, const BArgs& a);
 cudaError_t batch_dispatch_d2q9(BatchOp op, int dtype, const BArgs& a);
 cudaError_t batch_dispatch_d3q7(BatchOp op, int dtype, const BArgs& a);
+cudaError_t batch_dispatch_d3q15(BatchOp op, int dtype, const BArgs& a);
+cudaError_t batch_dispatch_d1q3(BatchOp op, int dtype, const BArgs& a);
+cudaError_t batch_dispatch_d2q4(BatchOp op, int dtype, const BArgs& a);
+cudaError_t batch_dispatch_d3q6(BatchOp op, int dtype, const BArgs& a);
 
 }  // namespace lbms

@@ -45,9 +45,6 @@ int lattice_dim(int lat)
     return lat == LBMS_D3Q7 || lat == LBMS_D3Q15 || lat == LBMS_D3Q6 ? 3 : (lat == LBMS_D1Q3 ? 1 : 2);
 }
 
-// The adjoint kernels treat population 0 as a rest population.
-bool adjoint_lattice(int lat) { return lat != LBMS_D2Q4 && lat != LBMS_D3Q6; }
-
 struct Layout {
     size_t f_bytes, off_f0, off_f1, off_partials, off_mass, off_status, off_bound, off_halo,
         halo_bytes, off_staging, staging_bytes, total;
@@ -289,7 +286,8 @@ cudaError_t adj_dispatch(const lbms_t* h, AdjOp op, const AArgs& a)
         case LBMS_D3Q7: return adj_dispatch_d3q7(op, h->dtype, a);
         case LBMS_D3Q15: return adj_dispatch_d3q15(op, h->dtype, a);
         case LBMS_D1Q3: return adj_dispatch_d1q3(op, h->dtype, a);
-        default: return cudaErrorInvalidValue;  // rejected by the entry points
+        case LBMS_D2Q4: return adj_dispatch_d2q4(op, h->dtype, a);
+        default: return adj_dispatch_d3q6(op, h->dtype, a);
     }
 }
 
@@ -867,7 +865,7 @@ int lbms_recompute(lbms_t* h, const void* f_in, long step, int count, void* f_ou
 
 size_t lbms_adjoint_scratch_size(const lbms_t* h)
 {
-    if (!h || h->halo || h->S > 4 || h->relax == LBMS_RELAX_FROZEN || !adjoint_lattice(h->lattice)) return 0;
+    if (!h || h->halo || h->S > 4 || h->relax == LBMS_RELAX_FROZEN) return 0;
     return (size_t)node_blocks(h->cells) * (kBlock / 32) * (h->n * (h->n - 1) / 2) * sizeof(double);
 }
 
@@ -877,7 +875,6 @@ int lbms_adjoint_seed(lbms_t* h, const void* grad_x, void* lam)
     if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
-    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!grad_x || !lam) return fail(h, LBMS_EINVAL, "grad_x and lam must not be NULL");
     if (!is_device_ptr(grad_x) || !is_device_ptr(lam))
         return fail(h, LBMS_EINVAL, "grad_x and lam must be device memory");
@@ -895,7 +892,6 @@ int lbms_adjoint_step(lbms_t* h, const void* f_prev, const void* lam_in, void* l
     if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
-    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!f_prev || !lam_in || !lam_out || !gacc)
         return fail(h, LBMS_EINVAL, "f_prev, lam_in, lam_out and gacc must not be NULL");
     if (lam_in == lam_out) return fail(h, LBMS_EINVAL, "lam_in and lam_out must be different buffers");
@@ -918,7 +914,6 @@ int lbms_adjoint_steps(lbms_t* h, const void* f_first, const void* f_rest, int c
     if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
-    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (count < 0) return fail(h, LBMS_EINVAL, "count = %d is negative", count);
     if (!f_first || !lam_a || !lam_b || !gacc || (count > 1 && !f_rest))
         return fail(h, LBMS_EINVAL, "f_first, f_rest (count > 1), lam_a, lam_b and gacc must not be NULL");
@@ -949,7 +944,6 @@ int lbms_adjoint_initial(lbms_t* h, const void* lam0, void* grad_x0)
     if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
-    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!lam0 || !grad_x0) return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must not be NULL");
     if (!is_device_ptr(lam0) || !is_device_ptr(grad_x0))
         return fail(h, LBMS_EINVAL, "lam0 and grad_x0 must be device memory");
@@ -967,7 +961,6 @@ int lbms_adjoint_reduce(lbms_t* h, const void* gacc, double* dL_dD)
     if (h->halo) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_HALO faces");
     if (h->S > 4) return fail(h, LBMS_EINVAL, "the adjoint supports up to 5 species");
     if (h->relax == LBMS_RELAX_FROZEN) return fail(h, LBMS_EINVAL, "the adjoint does not take LBMS_RELAX_FROZEN");
-    if (!adjoint_lattice(h->lattice)) return fail(h, LBMS_EINVAL, "the adjoint does not take D2Q4 or D3Q6");
     if (!gacc || !dL_dD) return fail(h, LBMS_EINVAL, "gacc and dL_dD must not be NULL");
     if (!is_device_ptr(gacc)) return fail(h, LBMS_EINVAL, "gacc must be device memory");
     const int np = h->n * (h->n - 1) / 2;

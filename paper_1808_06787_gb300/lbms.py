@@ -43,7 +43,8 @@ EXPORTED = (
     "lbms_last_error",
     "lbms_destroy",
     "lbms_batch_workspace_size", "lbms_batch_create", "lbms_batch_set_state", "lbms_batch_step",
-    "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_schedule",
+    "lbms_batch_moments", "lbms_batch_mass", "lbms_batch_status", "lbms_batch_set_boundary",
+    "lbms_batch_set_schedule",
     "lbms_batch_get_schedule", "lbms_batch_launches_per_step", "lbms_batch_tune",
     "lbms_batch_steps_done",
     "lbms_batch_last_error", "lbms_batch_destroy",
@@ -150,6 +151,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         L.lbms_batch_mass.restype = I
         L.lbms_batch_status.argtypes = [P, P]
         L.lbms_batch_status.restype = I
+        L.lbms_batch_set_boundary.argtypes = [P, I, I, P]
+        L.lbms_batch_set_boundary.restype = I
         L.lbms_batch_set_schedule.argtypes = [P, I]
         L.lbms_batch_set_schedule.restype = I
         L.lbms_batch_get_schedule.argtypes = [P]
@@ -543,12 +546,14 @@ class BatchSolver:
 
     ``grids``: list of (nx, ny[, nz]); ``Ds``: list (or array) of n x n
     diffusivity matrices; ``bcs``: None (all periodic) or a list of 6-tuples of
-    face kinds.  Fields are exchanged as lists of [n, nz, ny, nx] tensors or as
+    face kinds ("periodic", "noflux", "dirichlet"); ``boundary``:
+    {(instance, face): composition of all n species} for the Dirichlet faces.  Fields are exchanged as lists of [n, nz, ny, nx] tensors or as
     one packed 1-D tensor (instance after instance).
     """
 
     def __init__(self, lattice: str, Ds, grids, *, bcs=None, relax: str = "magic",
-                 dtype=torch.float32, device="cuda", stream: Optional[torch.cuda.Stream] = None):
+                 dtype=torch.float32, device="cuda", stream: Optional[torch.cuda.Stream] = None,
+                 boundary=None):
         if not torch.cuda.is_available():
             raise LbmsError("the lbms solver needs a CUDA device")
         L = load()
@@ -587,6 +592,16 @@ class BatchSolver:
             self._h = None
             raise LbmsError("lbms_batch_create: %s (%s)" % (ERRORS.get(rc, rc),
                                                             L.lbms_batch_last_error(None).decode()))
+        for (inst, face), xi_b in (boundary or {}).items():
+            self.set_boundary(inst, face, xi_b)
+
+    def set_boundary(self, instance: int, face: int, xi_b) -> None:
+        """Composition (all n species) held on Dirichlet face ``face`` of instance
+        ``instance`` (lbms_batch_set_boundary)."""
+        v = np.ascontiguousarray(np.asarray(xi_b, dtype=np.float64).reshape(-1))
+        _bcheck(self._h, load().lbms_batch_set_boundary(self._h, int(instance), int(face),
+                                                        v.ctypes.data_as(ctypes.c_void_p)),
+                "lbms_batch_set_boundary")
 
     def pack(self, fields) -> torch.Tensor:
         """Concatenate per-instance [n, nz, ny, nx] arrays into one flat tensor."""
@@ -594,11 +609,15 @@ class BatchSolver:
                  .reshape(-1).to(self.dtype) for f in fields]
         return torch.cat(parts)
 
-    def unpack(self, flat: torch.Tensor, per=1):
+    def unpack(self, flat: torch.Tensor, per=1, flux: bool = False):
+        """Per-instance views of a packed field: mole fractions [n, nz, ny, nx], or
+        with ``flux`` (or ``per`` > 1) fluxes [n, dim, nz, ny, nx] (``per`` = dim)."""
+        flux = flux or per > 1
+        per = self.dim if flux else per
         out = []
         for i, (nx, ny, nz) in enumerate(self.grids):
             a, b = int(self.offsets[i]) * per, int(self.offsets[i + 1]) * per
-            shape = (self.n, self.dim, nz, ny, nx) if per > 1 else (self.n, nz, ny, nx)
+            shape = (self.n, self.dim, nz, ny, nx) if flux else (self.n, nz, ny, nx)
             out.append(flat[a:b].view(shape))
         return out
 

@@ -48,6 +48,9 @@ def _one_step(s, f, step=0):
     ("D2Q9", 2, (12, 9, 1), (P,) * 6),
     ("D3Q15", 4, (7, 6, 5), (W, W, P, P, W, W)),
     ("D1Q3", 3, (33, 1, 1), (W, W, P, P, P, P)),
+    ("D2Q4", 3, (15, 13, 1), (W, W, P, P, P, P)),
+    ("D2Q4", 5, (12, 11, 1), (P,) * 6),
+    ("D3Q6", 4, (8, 7, 6), (P, P, W, W, W, W)),
 ])
 def test_adjoint_step_is_transpose_of_step_derivative(lattice, n, dims, bc):
     from paper_1808_06787_gb300 import Solver
@@ -421,3 +424,41 @@ def test_adjoint_steps_equal_single_adjoint_steps(dtype, count):
     out = lb if count % 2 else la
     assert torch.equal(out, a)
     assert torch.equal(gb, ga)
+
+
+@pytest.mark.parametrize("lattice,dims,bc", [("D2Q4", (24, 20, 1), (W, W, P, P, P, P)),
+                                             ("D3Q6", (10, 9, 8), (P, P, W, W, W, W))])
+def test_gradient_without_rest_velocity_matches_oracle_differences(lattice, dims, bc):
+    """Whole-run gradients on the lattices without a rest velocity (FP64, 300
+    steps) against fourth-order differences of the FP64 oracle."""
+    import oracle
+
+    from paper_1808_06787_gb300 import RunSpec, simulate
+
+    n, steps = 3, 300
+    x0 = sy.sin_modes(n, *dims, amp=0.1, seed=97)
+    # a target far from the start, so that the misfit (and the gradient) stand
+    # well above the rounding noise of the loss
+    target = oracle.run(lattice, _Dm((0.05, 0.12, 0.04)), x0, steps, bc=bc)
+    x0t = torch.from_numpy(x0).cuda().requires_grad_(True)
+    dp = torch.tensor(D_START, dtype=torch.float64, requires_grad=True)
+    xT = simulate(x0t, dp, RunSpec(lattice, dims, steps, bc=bc, dtype=torch.float64))
+    ((xT - torch.from_numpy(target).cuda()) ** 2).sum().backward()
+    loss = lambda d3, x: float(((oracle.run(lattice, _Dm(d3), x, steps, bc=bc) - target) ** 2).sum())
+    fds = []
+    for k in range(3):
+        def fun(e, k=k):
+            d = list(D_START)
+            d[k] += e
+            return loss(d, x0)
+
+        fds.append(_fd4(fun, 1e-4))
+    # the differences' rounding noise is set by the loss, the same for every
+    # component: the bound is relative to the largest component
+    scale = max(abs(v) for v in fds)
+    for k, fd in enumerate(fds):
+        assert abs(dp.grad[k].item() - fd) <= 1e-6 * scale + 1e-14, (k, dp.grad[k].item(), fd)
+    v = sy.small_mode([0.0, 0.0, 0.0], [1.0, -1.0, 0.0], 1.0, *dims, k=(1, 1, 0))
+    fd = _fd4(lambda e: loss(D_START, x0 + e * v), 1e-4)
+    ad = float((x0t.grad.cpu().numpy() * v).sum())
+    assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-14, (ad, fd)

@@ -27,8 +27,10 @@ def _cuda():
 
 def _mixed_batch(lattice, n, dtype, seed=5):
     g = sy.rng(seed)
-    if lattice == "D3Q7":
+    if lattice in ("D3Q7", "D3Q15", "D3Q6"):
         grids = [(9, 7, 5), (1, 1, 1), (16, 4, 3), (13, 13, 2), (3, 40, 1)]
+    elif lattice == "D1Q3":
+        grids = [(33, 1, 1), (1, 1, 1), (640, 1, 1), (51, 1, 1), (300, 1, 1), (7, 1, 1)]
     else:
         grids = [(33, 17, 1), (1, 1, 1), (64, 64, 1), (50, 3, 1), (5, 91, 1), (128, 20, 1)]
     Ds, bcs, x0s = [], [], []
@@ -50,7 +52,8 @@ def _single(lattice, D, x0, steps, bc, dtype):
     return x, J, s.mass()
 
 
-@pytest.mark.parametrize("lattice,n", [("D2Q5", 3), ("D2Q9", 5), ("D3Q7", 4)])
+@pytest.mark.parametrize("lattice,n", [("D2Q5", 3), ("D2Q9", 5), ("D3Q7", 4), ("D3Q15", 3),
+                                       ("D1Q3", 3), ("D2Q4", 3), ("D2Q4", 4), ("D3Q6", 3)])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
 def test_batch_equals_single_solves_bitwise(lattice, n, dtype):
     from paper_1808_06787_gb300 import BatchSolver
@@ -61,7 +64,7 @@ def test_batch_equals_single_solves_bitwise(lattice, n, dtype):
     steps = 77
     b.step(steps)
     x, J = b.moments(flux=True)
-    xs, Js = b.unpack(x), b.unpack(J, per=b.dim)
+    xs, Js = b.unpack(x), b.unpack(J, flux=True)
     mass = b.mass()
     assert b.status() == 0
     for i in range(len(grids)):
@@ -186,3 +189,58 @@ def test_batch_4096_uneven_d2q5_instances_full_size():
         x0 = sy.batch_field(i, int(grids[i][0]))
         ref = oracle.run("D2Q5", Ds[i], x0, 5000, bc=bcs[i])
         assert np.abs(xs[i].double().cpu().numpy().reshape(ref.shape) - ref).max() <= 2e-5, i
+
+
+@pytest.mark.parametrize("lattice", ["D2Q5", "D2Q4", "D3Q7", "D1Q3"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_batch_with_dirichlet_faces_equals_single_solves(lattice, dtype):
+    """Instances with Dirichlet faces (per-instance compositions) evolve bit for
+    bit as single solves with the same faces and compositions, with both kernel
+    shapes where the two-nodes-per-thread kernel exists."""
+    from paper_1808_06787_gb300 import BatchSolver, LbmsError, Solver
+
+    DI = "dirichlet"
+    n = 3
+    if lattice == "D3Q7":
+        grids = [(9, 7, 5), (6, 5, 8), (12, 3, 4)]
+        bcs = [(DI, DI, P, P, W, W), (W, W, DI, W, P, P), (P, P, P, P, DI, DI)]
+    elif lattice == "D1Q3":
+        grids = [(40, 1, 1), (77, 1, 1), (9, 1, 1)]
+        bcs = [(DI, DI, P, P, P, P), (DI, W, P, P, P, P), (W, DI, P, P, P, P)]
+    else:
+        grids = [(30, 17, 1), (21, 40, 1), (64, 9, 1)]
+        bcs = [(DI, DI, P, P, P, P), (W, W, DI, W, P, P), (DI, W, DI, DI, P, P)]
+    Ds = [sy.random_D(n, seed=600 + i) for i in range(3)]
+    x0s = [sy.sin_modes(n, *gr, amp=0.08, seed=610 + i) for i, gr in enumerate(grids)]
+    comps = sy.rng(620)
+    boundary = {}
+    for i, bc in enumerate(bcs):
+        for f, kind in enumerate(bc):
+            if kind == DI:
+                c = comps.uniform(0.1, 1.0, size=n)
+                boundary[(i, f)] = c / c.sum()
+    shapes = [0, 7] if (dtype == torch.float32 and lattice in ("D2Q5", "D2Q4", "D1Q3")) else [0]
+    steps = 61
+    for cand in shapes:
+        b = BatchSolver(lattice, Ds, grids, bcs=bcs, dtype=dtype)
+        with pytest.raises(LbmsError, match="no composition set"):
+            b.step(1)
+        for (i, f), c in boundary.items():
+            b.set_boundary(i, f, c)
+        b.set_schedule(cand)
+        b.set_state([torch.from_numpy(x) for x in x0s])
+        b.step(steps)
+        x, J = b.moments(flux=True)
+        xs, Js = b.unpack(x), b.unpack(J, flux=True)
+        for i in range(3):
+            bnd = {f: c for (j, f), c in boundary.items() if j == i}
+            s = Solver(lattice, Ds[i], grids[i], bc=bcs[i], dtype=dtype, boundary=bnd)
+            s.set_state(torch.from_numpy(x0s[i]).to(dtype).cuda())
+            s.step(steps)
+            xr, Jr = s.moments(flux=True)
+            assert torch.equal(xs[i], xr), (cand, i)
+            assert torch.equal(Js[i], Jr), (cand, i)
+        assert b.status() == 0
+        with pytest.raises(LbmsError, match="not a Dirichlet face"):
+            b.set_boundary(0, 5, [0.2, 0.3, 0.5])
+        b.close()

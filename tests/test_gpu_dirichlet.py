@@ -211,6 +211,8 @@ def test_linear_steady_state_and_stream_ordered_boundary_change(lattice, dims):
     ("D3Q7", 3, (9, 7, 6), (B, B, W, W, B, B)),
     ("D3Q15", 3, (7, 6, 5), (B, B, W, W, P, P)),
     ("D1Q3", 2, (30, 1, 1), (B, W, P, P, P, P)),
+    ("D2Q4", 3, (16, 12, 1), (B, B, W, W, P, P)),
+    ("D3Q6", 3, (8, 7, 6), (P, P, B, W, B, B)),
 ])
 def test_adjoint_step_with_dirichlet_faces_is_a_transpose(lattice, n, dims, bc):
     from paper_1808_06787_gb300 import Solver
@@ -266,11 +268,17 @@ def test_boundary_arguments_are_checked():
     s.set_boundary(0, (0.2, 0.3, 0.5))
     s.step(5)
     assert s.status() == 0
-    with pytest.raises(Exception):  # Dirichlet faces are not offered for batches
-        from paper_1808_06787_gb300 import BatchSolver
+    # batches: a Dirichlet face must have its composition before the first step
+    from paper_1808_06787_gb300 import BatchSolver
 
-        BatchSolver("D2Q5", np.stack([sy.random_D(3)]), np.array([[8, 8, 1]]),
-                    bcs=[(B, B, P, P, P, P)], dtype=torch.float32)
+    bt = BatchSolver("D2Q5", np.stack([sy.random_D(3)]), np.array([[8, 8, 1]]),
+                     bcs=[(B, B, P, P, P, P)], dtype=torch.float32)
+    with pytest.raises(LbmsError, match="no composition set"):
+        bt.step(1)
+    with pytest.raises(LbmsError, match="sums to"):
+        bt.set_boundary(0, 0, (0.2, 0.3, 0.6))
+    with pytest.raises(LbmsError, match="out of range"):
+        bt.set_boundary(1, 0, (0.2, 0.3, 0.5))
 
 
 def test_gradient_with_dirichlet_faces_matches_finite_differences():
