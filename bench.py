@@ -1039,6 +1039,7 @@ def run_reference(args, wl: Workload):
 
 
 def main():
+    global MIN_TIMED_S
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
@@ -1054,6 +1055,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-extras", action="store_true",
                     help="time only the headline workload (not the other parts of the metric)")
+    ap.add_argument("--min-timed-s", type=float, default=MIN_TIMED_S,
+                    help="repeat the timed region until this many seconds are timed (at least 5 "
+                         "repeats; profiling runs use 0)")
     ap.add_argument("--batch-schedule", type=int, default=-1,
                     help="batched workload: fixed step candidate (0..13: schedule + 7 x kernel "
                          "shape) instead of the tuner's")
@@ -1062,6 +1066,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    MIN_TIMED_S = max(0.0, args.min_timed_s)
     if args.workload != "adjoint" and args.steps is None:
         args.steps = 200
     if args.workload == "adjoint":

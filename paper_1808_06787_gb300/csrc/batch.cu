@@ -164,6 +164,7 @@ struct lbms_batch_s {
     void* xb_dev = nullptr;               // [count][6][S] Dirichlet compositions, solver dtype
     std::vector<uint32_t> dirichlet;      // per instance: Dirichlet face mask
     std::vector<uint32_t> xb_set;         // per instance: Dirichlet faces whose composition is set
+    bool any_dirichlet = false;
     uint32_t* status = nullptr;
     char* staging = nullptr;
     int fixed_shift = 32;
@@ -225,6 +226,7 @@ BArgs bargs(const lbms_batch_t* b, cudaStream_t st, uint32_t b0, uint32_t b1)
     a.status = b->status;
     a.field_off = b->foff_dev;
     a.xb = b->xb_dev;
+    a.dirichlet = b->any_dirichlet;
     a.stream = st;
     return a;
 }
@@ -442,6 +444,7 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
         ka.noflux = nf;
         ka.dirichlet = dr;
         b->dirichlet[c] = dr;
+        b->any_dirichlet |= dr != 0;
         BatchInst& d = b->inst[c];
         d.g = make_geom(ka);
         d.base = block * kBlock;

@@ -46,6 +46,7 @@ struct BArgs {
     const long long* field_off = nullptr;     // [count] element offset of instance i's x block
     int nodes_per_thread = 1;                 // plain steps: 1 or 2 (k_batch_step_pair)
     const void* xb = nullptr;                 // [count][6][S] Dirichlet compositions
+    bool dirichlet = false;                   // some instance has a Dirichlet face
     cudaStream_t stream = nullptr;
 };
 
@@ -74,11 +75,15 @@ struct BatchParams {
     T* x_out;
     T* J_out;
     const long long* field_off;
-    const T* __restrict__ xb;  // [count][6][S] Dirichlet compositions
 };
 
-template <int LAT, int S, typename T, bool MASS>
-__global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
+// DIR: some instance of the batch has Dirichlet faces (kernels of batches
+// without any are compiled without the anti-bounce-back code).
+// The Dirichlet compositions xb ([count][6][S]) are an argument of their own:
+// inside the parameter structure the extra member changed the register
+// allocation of the kernels that do not use it.
+template <int LAT, int S, typename T, bool MASS, bool DIR>
+__global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p, const T* __restrict__ xb)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
         plane.cells = p.total_nodes;  // the gather's plane stride
         const uint32_t cell = d.base + local;
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, plane, cell, h, f, p.xb + (size_t)id * 6 * S);
+        pull<LAT, S, T>(p.fin, plane, cell, h, f, DIR ? xb + (size_t)id * 6 * S : static_cast<const T*>(nullptr));
         mole_fractions<LAT, S, T>(f, xi);
         if (MASS) check_range<S, T>(xi, p.status);  // once per step call
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
@@ -116,8 +121,9 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p)
 // kBlock-node block of one instance; the pair's rest populations come in one
 // load and every plane goes out in one store.  Instance sizes may be odd: the
 // thread whose pair ends an odd instance takes its one node alone.
-template <int LAT, int S, typename T>
-__global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k_batch_step_pair(BatchParams<T> p)
+template <int LAT, int S, typename T, bool DIR>
+__global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value)
+    k_batch_step_pair(BatchParams<T> p, const T* __restrict__ xb)
 {
     using L = Lattice<LAT>;
     using V = typename Pair<T>::type;
@@ -151,7 +157,8 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k
         if (j == 1 && !both) break;
         const uint32_t local = local0 + j;
         const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
-        pull<LAT, S, T, REST>(p.fin, plane, c0 + j, h, f[j], p.xb + (size_t)id * 6 * S);
+        pull<LAT, S, T, REST>(p.fin, plane, c0 + j, h, f[j],
+                              DIR ? xb + (size_t)id * 6 * S : static_cast<const T*>(nullptr));
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f[j], xi);
         T L1[S][S], L2[S][S];
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_init(BatchParams<T> p)
 // Mole fractions (and fluxes) of every instance into its blocks of x_out (and
 // J_out, whose instance block starts at dim * field_off).
 template <int LAT, int S, typename T>
-__global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
+__global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p, const T* __restrict__ xb)
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_moments(BatchParams<T> p)
         Geom plane = d.g;
         plane.cells = p.total_nodes;
         T f[S][Q];
-        pull<LAT, S, T>(p.fin, plane, cell, h, f, p.xb + (size_t)id * 6 * S);
+        pull<LAT, S, T>(p.fin, plane, cell, h, f, xb + (size_t)id * 6 * S);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f, xi);
         const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
@@ -309,22 +316,33 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
     p.x_out = static_cast<T*>(a.field_x);
     p.J_out = static_cast<T*>(a.field_J);
     p.field_off = a.field_off;
-    p.xb = static_cast<const T*>(a.xb);
+    const T* xb = static_cast<const T*>(a.xb);
     const uint32_t blocks = a.block_end - a.block_begin;
     if (blocks == 0) return cudaSuccess;
     switch (op) {
         case BOP_STEP:
             if constexpr (pair_kernel_lattice<LAT, S, T>()) {
                 if (a.nodes_per_thread == 2) {
-                    k_batch_step_pair<LAT, S, T><<<blocks, kBlock / 2, 0, a.stream>>>(p);
+                    if (a.dirichlet)
+                        k_batch_step_pair<LAT, S, T, true><<<blocks, kBlock / 2, 0, a.stream>>>(p, xb);
+                    else
+                        k_batch_step_pair<LAT, S, T, false><<<blocks, kBlock / 2, 0, a.stream>>>(p, nullptr);
                     break;
                 }
             }
-            k_batch_step<LAT, S, T, false><<<blocks, kBlock, 0, a.stream>>>(p);
+            if (a.dirichlet)
+                k_batch_step<LAT, S, T, false, true><<<blocks, kBlock, 0, a.stream>>>(p, xb);
+            else
+                k_batch_step<LAT, S, T, false, false><<<blocks, kBlock, 0, a.stream>>>(p, nullptr);
             break;
-        case BOP_STEP_MASS: k_batch_step<LAT, S, T, true><<<blocks, kBlock, 0, a.stream>>>(p); break;
+        case BOP_STEP_MASS:
+            if (a.dirichlet)
+                k_batch_step<LAT, S, T, true, true><<<blocks, kBlock, 0, a.stream>>>(p, xb);
+            else
+                k_batch_step<LAT, S, T, true, false><<<blocks, kBlock, 0, a.stream>>>(p, nullptr);
+            break;
         case BOP_INIT: k_batch_init<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p); break;
-        case BOP_MOMENTS: k_batch_moments<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p); break;
+        case BOP_MOMENTS: k_batch_moments<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p, xb); break;
         default: k_batch_mass<LAT, S, T><<<blocks, kBlock, 0, a.stream>>>(p); break;
     }
     return cudaGetLastError();
