@@ -248,6 +248,30 @@ struct Pair<double> {
     using type = double2;
 };
 
+// The populations that move along y only, of the node pair (c0, c0 + 1) sharing a
+// row: one aligned pair load per species and population (see k_step_pair).
+template <int LAT, int S, typename T>
+__device__ __forceinline__ void load_pair_y(const T* __restrict__ fin, uint32_t plane_stride, uint32_t c0,
+                                            const Neighbourhood& h, T (&f)[2][S][Lattice<LAT>::Q])
+{
+    using L = Lattice<LAT>;
+    using V = typename Pair<T>::type;
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+        const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
+        if (cx != 0 || cz != 0 || cy == 0) continue;
+        const bool bounce = h.by[cy > 0 ? 0 : 1];
+        const uint32_t src = bounce ? c0 : (uint32_t)((int32_t)c0 + h.oy[cy > 0 ? 0 : 1]);
+        const size_t plane = (size_t)(bounce ? opp<LAT>(k) : k) * plane_stride;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const V v = *reinterpret_cast<const V*>(fin + (size_t)s * L::Q * plane_stride + plane + src);
+            f[0][s][k] = v.x;
+            f[1][s][k] = v.y;
+        }
+    }
+}
+
 template <int LAT, int S, typename T>
 struct PairOccupancy {
     static constexpr int value = S <= 1 ? 12 : 8;  // blocks of kBlock / 2 threads per SM
@@ -275,11 +299,20 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k
         }
     }
     const uint32_t hk = mix32(step * 0x9e3779b9u);
+    // with an even nx the pair shares a row, so its sources along y are an aligned
+    // pair too (offset +-nx or the row wrap, or both nodes bounce at a y wall)
+    const bool pair_y = L::DIM == 2 && (p.g.nx & 1) == 0;
+    Neighbourhood h[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) h[j] = neighbourhood<L::DIM, false>(p.g, c0 + j);
+    if (pair_y) load_pair_y<LAT, S, T>(p.fin, p.g.cells, c0, h[0], f);
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         const uint32_t cell = c0 + j;
-        const Neighbourhood h = neighbourhood<L::DIM, false>(p.g, cell);
-        pull<LAT, S, T, REST>(p.fin, p.g, cell, h, f[j], p.xb);
+        if (pair_y)
+            pull<LAT, S, T, REST, true>(p.fin, p.g, cell, h[j], f[j], p.xb);
+        else
+            pull<LAT, S, T, REST, false>(p.fin, p.g, cell, h[j], f[j], p.xb);
         T xi[S + 1];
         mole_fractions<LAT, S, T>(f[j], xi);
         T L1[S][S], L2[S][S];
