@@ -183,6 +183,14 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value)
     }
 }
 
+// Batches take the two-nodes-per-thread shape on the lattices with Q <= 5 (the
+// batched 3D lattices keep one node per thread).
+template <int LAT, int S, typename T>
+constexpr bool batch_pair_lattice()
+{
+    return Lattice<LAT>::Q <= 5 && S <= 2 && sizeof(T) == 4;
+}
+
 template <int LAT, int S, typename T>
 __global__ void __launch_bounds__(kBlock) k_batch_mass(BatchParams<T> p)
 {
@@ -321,7 +329,7 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
     if (blocks == 0) return cudaSuccess;
     switch (op) {
         case BOP_STEP:
-            if constexpr (pair_kernel_lattice<LAT, S, T>()) {
+            if constexpr (batch_pair_lattice<LAT, S, T>()) {
                 if (a.nodes_per_thread == 2) {
                     if (a.dirichlet)
                         k_batch_step_pair<LAT, S, T, true><<<blocks, kBlock / 2, 0, a.stream>>>(p, xb);

@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
     if (MASS) write_mass_partials<S>(xi, active, p.mass);
 }
 
-// Two nodes per thread (c, c + 1 with c even), for the light lattices whose
-// per-node instruction count rather than HBM bandwidth limits the one-node
-// kernel: the pair's rest populations (if the lattice has a rest velocity) come
+// Two nodes per thread (c, c + 1 with c even), for the lattices with Q <= 7 and
+// S <= 2 in FP32, whose per-node instruction count rather than HBM bandwidth
+// limits the one-node kernel: the pair's rest populations (if the lattice has a rest velocity) come
 // in one 8-byte load and every post-collision plane goes out in one 8-byte
 // store, and the per-thread
 // set-up is shared; the per-node arithmetic is that of k_step, so the results
@@ -248,8 +248,9 @@ struct Pair<double> {
     using type = double2;
 };
 
-// The populations that move along y only, of the node pair (c0, c0 + 1) sharing a
-// row: one aligned pair load per species and population (see k_step_pair).
+// The moving populations that do not move along x, of the node pair (c0, c0 + 1)
+// sharing a row (and a z-plane): one aligned pair load per species and population
+// (see k_step_pair).
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void load_pair_y(const T* __restrict__ fin, uint32_t plane_stride, uint32_t c0,
                                             const Neighbourhood& h, T (&f)[2][S][Lattice<LAT>::Q])
@@ -259,9 +260,12 @@ __device__ __forceinline__ void load_pair_y(const T* __restrict__ fin, uint32_t 
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
         const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
-        if (cx != 0 || cz != 0 || cy == 0) continue;
-        const bool bounce = h.by[cy > 0 ? 0 : 1];
-        const uint32_t src = bounce ? c0 : (uint32_t)((int32_t)c0 + h.oy[cy > 0 ? 0 : 1]);
+        if (cx != 0 || (cy == 0 && cz == 0)) continue;
+        int32_t off = 0;
+        bool bounce = false;
+        if (cy != 0) { off += h.oy[cy > 0 ? 0 : 1]; bounce |= h.by[cy > 0 ? 0 : 1]; }
+        if (cz != 0) { off += h.oz[cz > 0 ? 0 : 1]; bounce |= h.bz[cz > 0 ? 0 : 1]; }
+        const uint32_t src = bounce ? c0 : (uint32_t)((int32_t)c0 + off);
         const size_t plane = (size_t)(bounce ? opp<LAT>(k) : k) * plane_stride;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
@@ -299,9 +303,10 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k
         }
     }
     const uint32_t hk = mix32(step * 0x9e3779b9u);
-    // with an even nx the pair shares a row, so its sources along y are an aligned
-    // pair too (offset +-nx or the row wrap, or both nodes bounce at a y wall)
-    const bool pair_y = L::DIM == 2 && (p.g.nx & 1) == 0;
+    // with an even nx the pair shares a row, so its sources that do not move along
+    // x are an aligned pair too (offsets +-nx, +-nx ny or the wraps, or both nodes
+    // bounce at the same wall)
+    const bool pair_y = L::DIM >= 2 && (p.g.nx & 1) == 0;
     Neighbourhood h[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) h[j] = neighbourhood<L::DIM, false>(p.g, c0 + j);
@@ -340,7 +345,7 @@ constexpr uint32_t kPairMinCells = 1u << 21;
 template <int LAT, int S, typename T>
 constexpr bool pair_kernel_lattice()
 {
-    return Lattice<LAT>::Q <= 5 && S <= 2 && sizeof(T) == 4;
+    return Lattice<LAT>::Q <= 7 && S <= 2 && sizeof(T) == 4;
 }
 
 // Mass partials of the current (post-collision) state without stepping.

@@ -372,8 +372,8 @@ __device__ __forceinline__ int link_wall(int k, const Neighbourhood& h)
 // next to a Dirichlet face.
 // SKIP_REST: the caller has loaded the rest population (k = 0 of a lattice with
 // a rest velocity, which never moves) itself.  SKIP_Y: the caller has loaded the
-// populations that move along y only (the two-nodes-per-thread kernels pair
-// them); their Dirichlet correction below still applies.
+// moving populations that do not move along x (the two-nodes-per-thread kernels
+// pair them); their Dirichlet correction below still applies.
 template <int LAT, int S, typename T, bool SKIP_REST = false, bool SKIP_Y = false>
 __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, uint32_t cell,
                                      const Neighbourhood& h, T (&f)[S][Lattice<LAT>::Q],
@@ -386,7 +386,7 @@ __device__ __forceinline__ void pull(const T* __restrict__ fin, const Geom& g, u
 #pragma unroll
     for (int k = SKIP_REST ? 1 : 0; k < Q; ++k) {
         const int cx = L::cx(k), cy = L::cy(k), cz = L::cz(k);
-        if (SKIP_Y && cx == 0 && cz == 0 && cy != 0) continue;
+        if (SKIP_Y && cx == 0 && (cy != 0 || cz != 0)) continue;
         int32_t off = 0;
         bool bounce = false;
         if (cx != 0) { off += h.ox[cx > 0 ? 0 : 1]; bounce |= h.bx[cx > 0 ? 0 : 1]; }
