@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
 // set-up is shared; the per-node arithmetic is that of k_step, so the results
 // are the same bit for bit.  Blocks of kBlock / 2 threads cover kBlock nodes, the
 // partition of k_step.  Needs an even node count (so that every population plane
-// starts at an even node); no mass partials, no cut faces.
+// starts at an even node); no cut faces.
 template <typename T>
 struct Pair;
 template <>
@@ -281,60 +281,94 @@ struct PairOccupancy {
     static constexpr int value = S <= 1 ? 12 : 8;  // blocks of kBlock / 2 threads per SM
 };
 
-template <int LAT, int S, typename T>
+// Mass partials of a pair kernel's block (the block partition of k_step, so the
+// partials are the same integers): each thread adds its two nodes' fixed-point
+// values before the block reduction.
+template <int S>
+__device__ __forceinline__ void write_mass_partials_pair(const float (&xi)[2][S + 1], bool active,
+                                                         const MassOut& m)
+{
+    __shared__ long long red[kBlock / 32];
+    const float scale = __int_as_float((127 + m.shift) << 23);  // 2^shift, exact
+    long long* out = static_cast<long long*>(m.partials);
+#pragma unroll
+    for (int s = 0; s <= S; ++s) {
+        long long q = 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            q += __float2ll_rn((active ? fminf(fmaxf(xi[j][s], -4.0f), 4.0f) : 0.0f) * scale);
+        q = block_reduce_fixed(q, red);
+        if (threadIdx.x == 0) out[(size_t)blockIdx.x * (S + 1) + s] = q;
+    }
+}
+
+// MASS: the last step of a call, which also tests the mole fractions' range and
+// writes the mass partials (as k_step<..., true, ...>).
+template <int LAT, int S, typename T, bool MASS>
 __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value) k_step_pair(StepParams<T> p)
 {
     using L = Lattice<LAT>;
     using V = typename Pair<T>::type;
     constexpr int Q = L::Q;
     constexpr bool REST = L::K0 == 1;  // lattices without a rest velocity gather every population
+    static_assert(!MASS || sizeof(T) == 4, "the pair kernels are FP32");
     await_previous_grid();
     const uint32_t c0 = blockIdx.x * kBlock + 2 * threadIdx.x;
     const uint32_t step = *p.clock_in;
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.clock_out = step + 1;
-    if (c0 >= p.g.cells) return;  // cells is even: both nodes or neither
-    T f[2][S][Q];
-    if constexpr (REST) {
+    const bool active = c0 < p.g.cells;  // cells is even: both nodes or neither
+    T xs[2][S + 1];
+    if (!MASS && !active) return;
+    if (active) {
+        T f[2][S][Q];
+        if constexpr (REST) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.g.cells + c0);
-            f[0][s][0] = r.x;
-            f[1][s][0] = r.y;
+            for (int s = 0; s < S; ++s) {
+                const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.g.cells + c0);
+                f[0][s][0] = r.x;
+                f[1][s][0] = r.y;
+            }
         }
-    }
-    const uint32_t hk = mix32(step * 0x9e3779b9u);
-    // with an even nx the pair shares a row, so its sources that do not move along
-    // x are an aligned pair too (offsets +-nx, +-nx ny or the wraps, or both nodes
-    // bounce at the same wall)
-    const bool pair_y = L::DIM >= 2 && (p.g.nx & 1) == 0;
-    Neighbourhood h[2];
+        const uint32_t hk = mix32(step * 0x9e3779b9u);
+        // with an even nx the pair shares a row, so its sources that do not move along
+        // x are an aligned pair too (offsets +-nx, +-nx ny or the wraps, or both nodes
+        // bounce at the same wall)
+        const bool pair_y = L::DIM >= 2 && (p.g.nx & 1) == 0;
+        Neighbourhood h[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) h[j] = neighbourhood<L::DIM, false>(p.g, c0 + j);
-    if (pair_y) load_pair_y<LAT, S, T>(p.fin, p.g.cells, c0, h[0], f);
+        for (int j = 0; j < 2; ++j) h[j] = neighbourhood<L::DIM, false>(p.g, c0 + j);
+        if (pair_y) load_pair_y<LAT, S, T>(p.fin, p.g.cells, c0, h[0], f);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const uint32_t cell = c0 + j;
-        if (pair_y)
-            pull<LAT, S, T, REST, true>(p.fin, p.g, cell, h[j], f[j], p.xb);
-        else
-            pull<LAT, S, T, REST, false>(p.fin, p.g, cell, h[j], f[j], p.xb);
-        T xi[S + 1];
-        mole_fractions<LAT, S, T>(f[j], xi);
-        T L1[S][S], L2[S][S];
-        T xl[S + 1];
-        lambda_composition<S, T>(xi, p.co, p.relax, xl);
-        relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
-        collide<LAT, S, T>(f[j], xi, L1, L2, hk ^ (cell * 0x27d4eb2du));
-    }
+        for (int j = 0; j < 2; ++j) {
+            const uint32_t cell = c0 + j;
+            if (pair_y)
+                pull<LAT, S, T, REST, true>(p.fin, p.g, cell, h[j], f[j], p.xb);
+            else
+                pull<LAT, S, T, REST, false>(p.fin, p.g, cell, h[j], f[j], p.xb);
+            T xi[S + 1];
+            mole_fractions<LAT, S, T>(f[j], xi);
+            if (MASS) {
+                check_range<S, T>(xi, p.status);
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            V v;
-            v.x = f[0][s][k];
-            v.y = f[1][s][k];
-            *reinterpret_cast<V*>(p.fout + (size_t)(s * Q + k) * p.g.cells + c0) = v;
+                for (int s = 0; s <= S; ++s) xs[j][s] = xi[s];
+            }
+            T L1[S][S], L2[S][S];
+            T xl[S + 1];
+            lambda_composition<S, T>(xi, p.co, p.relax, xl);
+            relaxation_matrices<S, T>(xl, p.co.invD, T(1.0 / L::cs2()), p.relax, L1, L2);
+            collide<LAT, S, T>(f[j], xi, L1, L2, hk ^ (cell * 0x27d4eb2du));
         }
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                V v;
+                v.x = f[0][s][k];
+                v.y = f[1][s][k];
+                *reinterpret_cast<V*>(p.fout + (size_t)(s * Q + k) * p.g.cells + c0) = v;
+            }
+    }
+    if constexpr (MASS) write_mass_partials_pair<S>(xs, active, p.mass);
 }
 
 // Smallest grid stepped by the pair kernel: 2^21 nodes, whose populations
@@ -560,8 +594,12 @@ cudaError_t launch(Op op, const KArgs& a)
             if constexpr (pair_kernel_lattice<LAT, S, T>()) {
                 // grids whose state stays in L2 keep one node per thread (more
                 // threads for the latency-bound small grid)
-                if (op == OP_STEP && a.cells >= kPairMinCells && (a.cells & 1u) == 0)
-                    return launch_chained(k_step_pair<LAT, S, T>, blocks, kBlock / 2, a.stream, p);
+                if (a.cells >= kPairMinCells && (a.cells & 1u) == 0 && tb == kBlock) {
+                    if (op == OP_STEP)
+                        return launch_chained(k_step_pair<LAT, S, T, false>, blocks, kBlock / 2, a.stream, p);
+                    if (op == OP_STEP_MASS)
+                        return launch_chained(k_step_pair<LAT, S, T, true>, blocks, kBlock / 2, a.stream, p);
+                }
             }
             if (op == OP_STEP) return launch_chained(k_step<LAT, S, T, false, false>, blocks, tb, a.stream, p);
             if (op == OP_STEP_MASS) return launch_chained(k_step<LAT, S, T, true, false>, blocks, tb, a.stream, p);
