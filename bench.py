@@ -338,6 +338,25 @@ def timed_repeats(run_steps, stream, steps: int, barrier, min_repeats: int = 5):
     return statistics.median(times), times
 
 
+E2E_REPEATS = 5
+
+
+def e2e_median(run, barrier, repeats: int = E2E_REPEATS):
+    """Wall time of `run()` (host buffers in and out, so the host clock with a
+    barrier + synchronize on both sides): one untimed run, then the median of
+    `repeats` timed runs; returns (median s, list of s)."""
+    run()
+    barrier()
+    times = []
+    for _ in range(repeats):
+        barrier()
+        t0 = time.perf_counter()
+        run()
+        barrier()
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times), times
+
+
 def local_barrier():
     import torch
 
@@ -508,9 +527,7 @@ def run_ours(args, wl: Workload):
     x_host = torch.empty(field_shape, dtype=tdtype).pin_memory()
     e2e_s = None
     if not args.no_e2e:
-        with torch.cuda.stream(stream):
-            barrier()
-            t0 = time.perf_counter()
+        def e2e_run():
             s.set_state(x0_host)
             s.step(args.steps)
             if world > 1:
@@ -518,8 +535,9 @@ def run_ours(args, wl: Workload):
             else:
                 s.moments(x_host)
             s.mass()
-            barrier()
-            e2e_s = time.perf_counter() - t0
+
+        with torch.cuda.stream(stream):
+            e2e_s, _ = e2e_median(e2e_run, barrier)
     s.close()
     e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
     t_ms, e2e_ms = max_over_ranks(dist, [m["ms"], e2e_ms])
@@ -567,6 +585,7 @@ def run_ours(args, wl: Workload):
             "unit": "GLUPS",
             "h2d_bytes_per_step": round(x0_host.numel() * wl.es / args.steps, 1),
             "d2h_bytes_per_step": round((x_host.numel() * wl.es + 8 * wl.n) / args.steps, 1),
+            "timing": "host clock, median of %d runs after one untimed run" % E2E_REPEATS,
         },
         "gpu_launches": line["gpu_launches"],
         "clocks": clocks,
@@ -812,20 +831,22 @@ def measure_adjoint(warmup: int, local: int, n: int = 512, steps: int = ADJOINT_
         # end to end through the public API: pinned host x0 in, gradients back to the host
         x0_host = x0.cpu().pin_memory()
         g_host = torch.empty(x0.shape, dtype=torch.float32).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        xd = x0_host.cuda(non_blocking=True).requires_grad_(True)
-        dpe = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
-        le = ((simulate(xd, dpe, RunSpec("D2Q5", (n, n, 1), steps)).double() - target) ** 2).sum()
-        le.backward()
-        g_host.copy_(xd.grad, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - t0) * 1e3
+
+        def e2e_run():
+            xd = x0_host.cuda(non_blocking=True).requires_grad_(True)
+            dpe = torch.tensor((0.10, 0.08, 0.02), dtype=torch.float64, requires_grad=True)
+            le = ((simulate(xd, dpe, RunSpec("D2Q5", (n, n, 1), steps)).double() - target) ** 2).sum()
+            le.backward()
+            g_host.copy_(xd.grad, non_blocking=True)
+
+        e2e_s, _ = e2e_median(e2e_run, torch.cuda.synchronize, repeats=3)
+        e2e_ms = e2e_s * 1e3
         out["e2e"] = {
             "value": round(e2e_ms / t_fwd, 3),
             "unit": "x forward",
             "h2d_bytes_per_step": round(x0_host.numel() * 4 / steps, 1),
             "d2h_bytes_per_step": round((g_host.numel() * 4 + 3 * 8) / steps, 1),
+            "timing": "host clock, median of 3 gradient runs after one untimed run",
         }
     return out
 
@@ -849,15 +870,14 @@ def run_batch(args):
     grids, Ds, bcs = m.pop("grids"), m.pop("Ds"), m.pop("bcs")
     e2e_s = None
     if not args.no_e2e:
-        with torch.cuda.stream(stream):
-            barrier()
-            t0 = time.perf_counter()
+        def e2e_run():
             b.set_state(x0_host)
             b.step(args.steps)
             b.moments(out_device="cpu")
             b.mass()
-            barrier()
-            e2e_s = time.perf_counter() - t0
+
+        with torch.cuda.stream(stream):
+            e2e_s, _ = e2e_median(e2e_run, barrier)
     b.close()
     e2e_ms = e2e_s * 1e3 if e2e_s is not None else float("nan")
     t_ms, e2e_ms = max_over_ranks(dist, [m["ms_per_step"] * args.steps, e2e_ms])
@@ -887,6 +907,7 @@ def run_batch(args):
             "unit": "solves/s",
             "h2d_bytes_per_step": round(x0_host.numel() * 4 / args.steps, 1),
             "d2h_bytes_per_step": round((x0_host.numel() * 4 + 8 * 3 * count) / args.steps, 1),
+            "timing": "host clock, median of %d runs after one untimed run" % E2E_REPEATS,
         },
         "cpu_baseline": None if (args.no_cpu_baseline or world > 1)
         else cpu_baseline_batch(grids, Ds, bcs, 1004 + rank, budget_s=args.cpu_budget),

@@ -539,7 +539,7 @@ cudaError_t adj_launch(AdjOp op, const AArgs& a)
         p.g = make_geom(a.k);
         p.relax = a.k.relax;
         p.xb = static_cast<const T*>(a.k.xb);
-        p.co = make_coeffs<T>(a.k);
+        p.co = make_coeffs<T>(a.k, 1.0);
         return launch_chained(k_adjoint_step<LAT, S, T>, blocks, kBlock, a.k.stream, p);
     }
     AdjFieldParams<T> p;

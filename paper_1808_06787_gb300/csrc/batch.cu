@@ -155,7 +155,8 @@ struct lbms_batch_s {
     int cur = 0;
     void* partials = nullptr;
     double* mass_dev = nullptr;
-    bool mass_valid = false;
+    bool partials_valid = false;  // the mass partials are those of the current state
+    bool mass_valid = false;      // mass_dev holds their reduction
     BatchInst* inst_dev = nullptr;
     uint32_t* blk_dev = nullptr;
     void* invD_dev = nullptr;
@@ -459,7 +460,8 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
         const double* Dc = D + (size_t)c * n * n;
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) {
-                const double v = i == j ? 0.0 : 1.0 / Dc[i * n + j];
+                // halved inverse diffusivities (relaxation_matrices takes 1/(2 D_ij))
+                const double v = i == j ? 0.0 : 0.5 * (1.0 / Dc[i * n + j]);
                 const size_t at = ((size_t)c * n * n + i * n + j);
                 if (dtype == LBMS_F64)
                     reinterpret_cast<double*>(invD.data())[at] = v;
@@ -504,6 +506,7 @@ int lbms_batch_set_state(lbms_batch_t* b, const void* x0, const int64_t* offsets
     if (e != cudaSuccess) return bcuda(b, e, "cudaMemsetAsync");
     b->cur = 0;
     b->steps = 0;
+    b->partials_valid = false;
     b->mass_valid = false;
     const long long* uoff = user_offsets(b, offsets);
     BArgs a = bargs(b, b->stream, 0, b->lay.total_blocks);
@@ -591,9 +594,9 @@ int lbms_batch_step(lbms_batch_t* b, long n_steps)
     if (e != cudaSuccess) return bcuda(b, e, "batch step kernel");
     b->cur = 1 - b->cur;
     ++b->steps;
-    e = bfinalize(b, b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "batch mass reduction");
-    b->mass_valid = true;
+    // the reduction of the partials waits for lbms_batch_mass
+    b->partials_valid = true;
+    b->mass_valid = false;
     return LBMS_OK;
 }
 
@@ -665,12 +668,17 @@ int lbms_batch_mass(lbms_batch_t* b, double* mass_out)
     if (!mass_out) return bfail(b, LBMS_EINVAL, "mass_out is NULL");
     b->err[0] = '\0';
     cudaError_t e;
-    if (!b->mass_valid) {
+    if (!b->partials_valid) {
         BArgs a = bargs(b, b->stream, 0, b->lay.total_blocks);
         a.fout = b->f[b->cur];
         e = bdispatch(b, BOP_MASS, a);
-        if (e == cudaSuccess) e = bfinalize(b, b->stream);
-        if (e != cudaSuccess) return bcuda(b, e, "batch mass kernels");
+        if (e != cudaSuccess) return bcuda(b, e, "batch mass kernel");
+        b->partials_valid = true;
+        b->mass_valid = false;
+    }
+    if (!b->mass_valid) {
+        e = bfinalize(b, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "batch mass reduction");
         b->mass_valid = true;
     }
     e = cudaMemcpyAsync(mass_out, b->mass_dev, sizeof(double) * b->count * b->n, cudaMemcpyDeviceToHost,

@@ -32,7 +32,7 @@ struct BArgs {
     uint32_t block_begin = 0, block_end = 0;  // global block range of this launch
     const uint32_t* blk_inst = nullptr;       // [total_blocks] instance of each block
     const BatchInst* inst = nullptr;          // [count]
-    const void* invD = nullptr;               // [count][n][n] of the element type
+    const void* invD = nullptr;               // [count][n][n] 1/(2 D_ij), element type
     int n_species = 2;
     int relax = LBMS_RELAX_MAGIC;
     uint32_t* clock = nullptr;                // [count][2] step counters

@@ -12,7 +12,7 @@ namespace lbms {
 
 template <typename T>
 struct Coeffs {
-    T invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES];
+    T invD[LBMS_MAX_SPECIES][LBMS_MAX_SPECIES];  // 1/D_ij times make_coeffs' scale
     T xref[LBMS_MAX_SPECIES];  // reference composition of LBMS_RELAX_FROZEN
 };
 
@@ -514,12 +514,14 @@ __global__ void __launch_bounds__(kBlock) k_moments(FieldParams<T> p)
             for (int a = 0; a < DIM; ++a) p.G_out[((size_t)s * DIM + a) * p.stride + i] = G[s][a];
 }
 
+// `scale` multiplies the inverse diffusivities: 0.5 for the kernels that take
+// the halved ones (relaxation_matrices), 1 for the adjoint.
 template <typename T>
-Coeffs<T> make_coeffs(const KArgs& a)
+Coeffs<T> make_coeffs(const KArgs& a, double scale)
 {
     Coeffs<T> c;
     for (int i = 0; i < LBMS_MAX_SPECIES; ++i) {
-        for (int j = 0; j < LBMS_MAX_SPECIES; ++j) c.invD[i][j] = (T)a.invD[i][j];
+        for (int j = 0; j < LBMS_MAX_SPECIES; ++j) c.invD[i][j] = (T)(scale * a.invD[i][j]);
         c.xref[i] = (T)a.xref[i];
     }
     return c;
@@ -581,7 +583,7 @@ cudaError_t launch(Op op, const KArgs& a)
         p.clock_out = a.clock_out;
         p.xb = static_cast<const T*>(a.xb);
         p.halo = make_halo<T>(a);
-        p.co = make_coeffs<T>(a);
+        p.co = make_coeffs<T>(a, 0.5);
         const uint32_t tb = a.step_block;
         const uint32_t blocks = (a.cells + tb - 1) / tb;
         if constexpr (HALO_STEPS) {
@@ -623,7 +625,7 @@ cudaError_t launch(Op op, const KArgs& a)
         p.status = a.status;
         p.xb = static_cast<const T*>(a.xb);
         p.halo = make_halo<T>(a);
-        p.co = make_coeffs<T>(a);
+        p.co = make_coeffs<T>(a, 0.5);
         const uint32_t blocks = node_blocks(a.c1 - a.c0);
         if (blocks == 0) return cudaSuccess;
         if (op == OP_INIT)

@@ -24,6 +24,11 @@ constexpr int kGraphSteps = 32;                   // steps per captured graph (e
 // captured run lengths: full runs of kGraphSteps, then the even remainder in
 // binary pieces (all even, so a run leaves the buffer parity unchanged)
 constexpr int kGraphLens[5] = {kGraphSteps, 16, 8, 4, 2};
+// calls of at most kCallGraphMax steps are replayed whole: the plain steps and
+// the mass-writing last one in one graph, kept for the kCallGraphs most
+// recently used (length, parity) pairs
+constexpr long kCallGraphMax = 64;
+constexpr int kCallGraphs = 4;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -242,6 +247,13 @@ struct lbms_s {
     cudaStream_t capture = nullptr;
     // captured runs of kGraphLens[j] plain steps starting from buffer parity p
     cudaGraphExec_t graph[2][5] = {};
+    struct CallGraph {
+        long n = 0;      // steps of the call
+        int parity = 0;  // buffer parity it starts from
+        unsigned long long used = 0;
+        cudaGraphExec_t exec = nullptr;
+    } call_graph[kCallGraphs];
+    unsigned long long call_tick = 0;
     bool graphs_ok = true;
     long steps = 0;
     char err[512] = "";
@@ -341,6 +353,70 @@ cudaError_t launch_finalize(const lbms_t* h, cudaStream_t st)
 }
 
 // Capture kGraphSteps plain steps starting from buffer `parity`.
+// The captured graphs hold the kernel arguments: dropped whenever those change.
+void drop_graphs(lbms_t* h)
+{
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 5; ++j)
+            if (h->graph[i][j]) {
+                cudaGraphExecDestroy(h->graph[i][j]);
+                h->graph[i][j] = nullptr;
+            }
+    for (auto& c : h->call_graph) {
+        if (c.exec) cudaGraphExecDestroy(c.exec);
+        c = lbms_t::CallGraph{};
+    }
+}
+
+// One whole call: n - 1 plain steps and the mass-writing one from parity p.
+cudaError_t build_call_graph(lbms_t* h, long n, int parity, cudaGraphExec_t* out)
+{
+    cudaError_t e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    int src = parity;
+    for (long i = 0; i < n && le == cudaSuccess; ++i) {
+        le = launch_step(h, src, i == n - 1, h->capture);
+        src = 1 - src;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->capture, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// The graph of a call of n steps from the current parity (built on first use,
+// replacing the least recently used one), or null when it cannot be captured.
+cudaGraphExec_t call_graph_for(lbms_t* h, long n)
+{
+    lbms_t::CallGraph* slot = &h->call_graph[0];
+    for (auto& c : h->call_graph) {
+        if (c.exec && c.n == n && c.parity == h->cur) {
+            c.used = ++h->call_tick;
+            return c.exec;
+        }
+        if (c.used < slot->used) slot = &c;
+    }
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    *slot = lbms_t::CallGraph{};
+    cudaGraphExec_t g = nullptr;
+    if (build_call_graph(h, n, h->cur, &g) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    slot->n = n;
+    slot->parity = h->cur;
+    slot->used = ++h->call_tick;
+    slot->exec = g;
+    return g;
+}
+
 cudaError_t build_graph(lbms_t* h, int parity, int j)
 {
     cudaError_t e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
@@ -622,13 +698,7 @@ int lbms_set_reference(lbms_t* h, const double* xi_ref)
     h->err[0] = '\0';
     for (int s = 0; s < h->n; ++s) h->xref[s] = xi_ref[s];
     h->xref_set = true;
-    // the captured step graphs carry the kernel arguments: capture them again
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 5; ++j)
-            if (h->graph[i][j]) {
-                cudaGraphExecDestroy(h->graph[i][j]);
-                h->graph[i][j] = nullptr;
-            }
+    drop_graphs(h);
     return LBMS_OK;
 }
 
@@ -651,6 +721,18 @@ int lbms_step(lbms_t* h, long n_steps)
     cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
     const bool use_graphs = h->graphs_ok && cs == cudaStreamCaptureStatusNone;
+    if (use_graphs && n_steps >= 2 && n_steps <= kCallGraphMax) {
+        cudaGraphExec_t g = call_graph_for(h, n_steps);
+        if (g) {
+            e = cudaGraphLaunch(g, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            if (n_steps & 1) h->cur = 1 - h->cur;
+            h->steps += n_steps;
+            h->partials_valid = true;
+            h->mass_valid = false;
+            return LBMS_OK;
+        }
+    }
     long left = n_steps;  // the last step also writes the mass partials
     for (int j = 0; use_graphs && j < 5; ++j) {
         while (left - 1 >= kGraphLens[j] && use_graphs) {
@@ -991,12 +1073,7 @@ int lbms_set_subdomain(lbms_t* h, long first_layer)
     h->err[0] = '\0';
     // node indices of the undivided grid (modulo 2^32, as the rounding key takes them)
     h->origin = (uint32_t)((uint64_t)first_layer * h->plane);
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 5; ++j)
-            if (h->graph[i][j]) {
-                cudaGraphExecDestroy(h->graph[i][j]);
-                h->graph[i][j] = nullptr;
-            }
+    drop_graphs(h);
     return LBMS_OK;
 }
 
@@ -1081,9 +1158,7 @@ const char* lbms_last_error(const lbms_t* h) { return h ? h->err : g_create_erro
 void lbms_destroy(lbms_t* h)
 {
     if (!h) return;
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 5; ++j)
-            if (h->graph[i][j]) cudaGraphExecDestroy(h->graph[i][j]);
+    drop_graphs(h);
     if (h->capture) cudaStreamDestroy(h->capture);
     delete h;
 }

@@ -13,12 +13,20 @@
 // spread over four decades; the test-suite checks that property.
 // Lambda_2 follows Eq. 3-16, or equals Lambda_1 for SRT.
 //
+// Half matrices.  The step kernels carry Lambda_1/2 and Lambda_2/2: they take
+// the inverse diffusivities halved, 1/(2 D_ij), so Eq. 2-10 (linear in them)
+// yields B/2 directly, K = I/c_s^2 + B/2 needs no scaling, K^{-1} (B/2) is
+// Lambda_1/2, and Eq. 3-16 rewritten for l/2 gives Lambda_2/2.  Scaling by a
+// power of two is exact, so these are the halves of the unscaled matrices bit
+// for bit; the halves of the pair form below fold into them.
+//
 // Collision.  For moment bases whose rows are the total mass, odd-order rows
 // (relaxed by Lambda_1) and even-order rows (relaxed by Lambda_2), the
 // moment-space collision of Eq. 3-13a equals the pair form used here: for each
 // opposite pair (k, kbar) with g = f - w xi,
 //     s = (g_k + g_kbar)/2,  a = (g_k - g_kbar)/2,
 //     f+_k = f_k - Lambda_2 s - Lambda_1 a,  f+_kbar = f_k - Lambda_2 s + Lambda_1 a,
+// evaluated as (Lambda_2/2)(g_k + g_kbar) and (Lambda_1/2)(g_k - g_kbar),
 // and for the rest population f+_0 = f_0 - Lambda_2 g_0.  Sec. 3.1 notes that
 // odd/even relaxation groups make the MRT model a two-relaxation-time model.
 //
@@ -50,10 +58,11 @@ namespace lbms {
 __device__ __forceinline__ float recip(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 
-// Lambda_1 = K^{-1} B and Lambda_2 (Eq. 3-16, or = Lambda_1 for SRT) from all S+1
-// mole fractions.
+// Lambda_1/2 = K^{-1} (B/2) and Lambda_2/2 (Eq. 3-16, or = Lambda_1/2 for SRT) from
+// all S+1 mole fractions and the halved inverse diffusivities invDh[i][j] =
+// 1/(2 D_ij).
 template <int S, typename T, typename InvD>
-__device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const InvD& invD,
+__device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const InvD& invDh,
                                                     T cs2inv, int relax, T (&L1)[S][S],
                                                     T (&L2)[S][S])
 {
@@ -62,22 +71,22 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
     for (int i = 0; i < S; ++i) {
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            T b;
+            T b;  // B/2
             if (i != j) {
-                b = xi[i] * (invD[i][S] - invD[i][j]);  // Eq. 2-10, i != j
+                b = xi[i] * (invDh[i][S] - invDh[i][j]);  // Eq. 2-10, i != j
             } else {
-                b = xi[i] * invD[i][S];  // Eq. 2-10, i == j
+                b = xi[i] * invDh[i][S];  // Eq. 2-10, i == j
 #pragma unroll
                 for (int k = 0; k <= S; ++k)
-                    if (k != i) b += xi[k] * invD[i][k];
+                    if (k != i) b += xi[k] * invDh[i][k];
             }
             L1[i][j] = b;
-            K[i][j] = T(0.5) * b + (i == j ? cs2inv : T(0));
+            K[i][j] = i == j ? b + cs2inv : b;
         }
     }
     if constexpr (S == 2) {
-        // ternary mixtures (Remark IV): Lambda_1 = adj(K) B / det(K), one reciprocal;
-        // det(K) > 0 because B's eigenvalues are real and non-negative
+        // ternary mixtures (Remark IV): Lambda_1/2 = adj(K) (B/2) / det(K), one
+        // reciprocal; det(K) > 0 because B's eigenvalues are real and non-negative
         const T rdet = recip(K[0][0] * K[1][1] - K[0][1] * K[1][0]);
         const T b00 = L1[0][0], b01 = L1[0][1], b10 = L1[1][0], b11 = L1[1][1];
         L1[0][0] = (K[1][1] * b00 - K[0][1] * b10) * rdet;
@@ -110,17 +119,18 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
 #pragma unroll
         for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
     if (relax != LBMS_RELAX_SRT) {  // Eq. 3-16 (the frozen mode uses it too)
+        // Eq. 3-16 with l = 2 h: lambda_2/2 = 4 (h - 1) / (h - 4)
         if constexpr (S == 2) {
-            // Eq. 3-16 for both diagonal entries with one reciprocal
-            const T a = L1[0][0] - T(8), b = L1[1][1] - T(8);
+            // both diagonal entries with one reciprocal
+            const T a = L1[0][0] - T(4), b = L1[1][1] - T(4);
             const T r = recip(a * b);
-            L2[0][0] = T(8) * (L1[0][0] - T(2)) * (b * r);
-            L2[1][1] = T(8) * (L1[1][1] - T(2)) * (a * r);
+            L2[0][0] = T(4) * (L1[0][0] - T(1)) * (b * r);
+            L2[1][1] = T(4) * (L1[1][1] - T(1)) * (a * r);
         } else {
 #pragma unroll
             for (int i = 0; i < S; ++i) {
-                const T l = L1[i][i];
-                L2[i][i] = T(8) * (l - T(2)) * recip(l - T(8));  // Eq. 3-16, i == j
+                const T h = L1[i][i];
+                L2[i][i] = T(4) * (h - T(1)) * recip(h - T(4));  // Eq. 3-16, i == j
             }
         }
     }
@@ -179,12 +189,12 @@ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
     e = (a - (s - bp)) + (b - bp);
 }
 
-// In-place collision in the pair form (see the header comment); `key` (distinct
-// per node and step) seeds the stochastic rounding of the rest population
-// (FP32 only).
+// In-place collision in the pair form (see the header comment) with the half
+// matrices L1h = Lambda_1/2, L2h = Lambda_2/2; `key` (distinct per node and
+// step) seeds the stochastic rounding of the rest population (FP32 only).
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi)[S + 1],
-                                        const T (&L1)[S][S], const T (&L2)[S][S], uint32_t key)
+                                        const T (&L1h)[S][S], const T (&L2h)[S][S], uint32_t key)
 {
     using L = Lattice<LAT>;
     // sum of the moving populations' increments f_k - f+_k (each exact: f+_k is
@@ -195,20 +205,20 @@ __device__ __forceinline__ void collide(T (&f)[S][Lattice<LAT>::Q], const T (&xi
 #pragma unroll
     for (int pr = 0; pr < L::NPAIR; ++pr) {
         const int ka = L::K0 + 2 * pr, kb = ka + 1;
-        const T wp = T(L::w(ka));
-        T sym[S], asym[S];
+        const T wp2 = T(2.0 * L::w(ka));
+        T sym[S], asym[S];  // g_k + g_kbar and g_k - g_kbar
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            sym[j] = T(0.5) * (f[j][ka] + f[j][kb]) - wp * xi[j];
-            asym[j] = T(0.5) * (f[j][ka] - f[j][kb]);
+            sym[j] = (f[j][ka] + f[j][kb]) - wp2 * xi[j];
+            asym[j] = f[j][ka] - f[j][kb];
         }
 #pragma unroll
         for (int i = 0; i < S; ++i) {
             T ds = T(0), da = T(0);
 #pragma unroll
             for (int j = 0; j < S; ++j) {
-                ds += L2[i][j] * sym[j];
-                da += L1[i][j] * asym[j];
+                ds += L2h[i][j] * sym[j];
+                da += L1h[i][j] * asym[j];
             }
             const T na = f[i][ka] - (ds + da);
             const T nb = f[i][kb] - (ds - da);
@@ -449,13 +459,13 @@ __device__ __forceinline__ void pack_halo(const T (&f)[S][Lattice<LAT>::Q], cons
     }
 }
 
-// From the pre-collision populations f at a node and its Lambda_1: the fluxes
-// J = (I - Lambda_1/2) m_1 (Eq. 2-12 with Eq. 3-26) and the local gradients
-// grad xi = -Lambda_1 m_1 / c_s^2 (Eq. xix), m_1 = sum_k c_k f_k; the last
-// species' rows close the sums (Eq. 2-3a).
+// From the pre-collision populations f at a node and its L1h = Lambda_1/2: the
+// fluxes J = (I - Lambda_1/2) m_1 (Eq. 2-12 with Eq. 3-26) and the local
+// gradients grad xi = -Lambda_1 m_1 / c_s^2 (Eq. xix), m_1 = sum_k c_k f_k; the
+// last species' rows close the sums (Eq. 2-3a).
 template <int LAT, int S, typename T>
 __device__ __forceinline__ void flux_and_gradient(const T (&f)[S][Lattice<LAT>::Q],
-                                                  const T (&L1)[S][S],
+                                                  const T (&L1h)[S][S],
                                                   T (&J)[S + 1][Lattice<LAT>::DIM],
                                                   T (&G)[S + 1][Lattice<LAT>::DIM])
 {
@@ -482,12 +492,12 @@ __device__ __forceinline__ void flux_and_gradient(const T (&f)[S][Lattice<LAT>::
     for (int s = 0; s < S; ++s)
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            T lm = T(0);
+            T lm = T(0);  // (Lambda_1 m_1)/2
 #pragma unroll
-            for (int j = 0; j < S; ++j) lm += L1[s][j] * m1[j][a];
-            J[s][a] = m1[s][a] - T(0.5) * lm;
+            for (int j = 0; j < S; ++j) lm += L1h[s][j] * m1[j][a];
+            J[s][a] = m1[s][a] - lm;
             J[S][a] -= J[s][a];
-            G[s][a] = -lm * T(1.0 / L::cs2());
+            G[s][a] = -lm * T(2.0 / L::cs2());
             G[S][a] -= G[s][a];
         }
 }
