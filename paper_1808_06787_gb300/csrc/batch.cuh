@@ -121,8 +121,14 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p, const T
 // kBlock-node block of one instance; the pair's rest populations come in one
 // load and every plane goes out in one store.  Instance sizes may be odd: the
 // thread whose pair ends an odd instance takes its one node alone.
-template <int LAT, int S, typename T, bool DIR>
-__global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value)
+// 12 blocks of kBlock / 2 threads per SM (40 registers; on ternary D2Q5 with a
+// 16-byte spill, which still measured 3 % faster than 10 blocks at 48 registers:
+// the instance lookup at the start of every block leaves a latency that more
+// resident blocks hide).  MASS: the last step of a call, which also tests the
+// range and writes the block's mass partials (the 256-node blocks of
+// k_batch_step, so the same integers).
+template <int LAT, int S, typename T, bool DIR, bool MASS>
+__global__ void __launch_bounds__(kBlock / 2, 12)
     k_batch_step_pair(BatchParams<T> p, const T* __restrict__ xb)
 {
     using L = Lattice<LAT>;
@@ -136,51 +142,65 @@ __global__ void __launch_bounds__(kBlock / 2, PairOccupancy<LAT, S, T>::value)
     uint32_t* clk = p.clock + 2 * id;
     const uint32_t step = clk[p.parity];
     if (blk == d.block0 && threadIdx.x == 0) clk[1 - p.parity] = step + 1;
-    if (local0 >= d.g.cells) return;
-    const bool both = local0 + 1 < d.g.cells;
-    Geom plane = d.g;
-    plane.cells = p.total_nodes;  // the gather's plane stride
-    const uint32_t c0 = d.base + local0;
-    const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
-    const uint32_t hk = mix32(step * 0x9e3779b9u);
-    T f[2][S][Q];
-    if constexpr (REST) {
+    const bool active = local0 < d.g.cells;
+    if (!MASS && !active) return;
+    T xs[2][S + 1];  // MASS: the pair's mole fractions, zero where it has no node
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.total_nodes + c0);
-            f[0][s][0] = r.x;
-            f[1][s][0] = r.y;
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int s = 0; s <= S; ++s) xs[j][s] = T(0);
+    if (active) {
+        const bool both = local0 + 1 < d.g.cells;
+        Geom plane = d.g;
+        plane.cells = p.total_nodes;  // the gather's plane stride
+        const uint32_t c0 = d.base + local0;
+        const InvDView<T> iv{p.invD + (size_t)id * (S + 1) * (S + 1), S + 1};
+        const uint32_t hk = mix32(step * 0x9e3779b9u);
+        T f[2][S][Q];
+        if constexpr (REST) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const V r = *reinterpret_cast<const V*>(p.fin + (size_t)(s * Q) * p.total_nodes + c0);
+                f[0][s][0] = r.x;
+                f[1][s][0] = r.y;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (j == 1 && !both) break;
+            const uint32_t local = local0 + j;
+            const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
+            pull<LAT, S, T, REST>(p.fin, plane, c0 + j, h, f[j],
+                                  DIR ? xb + (size_t)id * 6 * S : static_cast<const T*>(nullptr));
+            T xi[S + 1];
+            mole_fractions<LAT, S, T>(f[j], xi);
+            if (MASS) {
+                check_range<S, T>(xi, p.status);
+#pragma unroll
+                for (int s = 0; s <= S; ++s) xs[j][s] = xi[s];
+            }
+            T L1[S][S], L2[S][S];
+            relaxation_matrices<S, T>(xi, iv, T(1.0 / L::cs2()), p.relax, L1, L2);
+            collide<LAT, S, T>(f[j], xi, L1, L2, hk ^ (local * 0x27d4eb2du));
+        }
+        if (both) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    V v;
+                    v.x = f[0][s][k];
+                    v.y = f[1][s][k];
+                    *reinterpret_cast<V*>(p.fout + (size_t)(s * Q + k) * p.total_nodes + c0) = v;
+                }
+        } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + c0] = f[0][s][k];
         }
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        if (j == 1 && !both) break;
-        const uint32_t local = local0 + j;
-        const Neighbourhood h = neighbourhood<Lattice<LAT>::DIM, false>(d.g, local);
-        pull<LAT, S, T, REST>(p.fin, plane, c0 + j, h, f[j],
-                              DIR ? xb + (size_t)id * 6 * S : static_cast<const T*>(nullptr));
-        T xi[S + 1];
-        mole_fractions<LAT, S, T>(f[j], xi);
-        T L1[S][S], L2[S][S];
-        relaxation_matrices<S, T>(xi, iv, T(1.0 / L::cs2()), p.relax, L1, L2);
-        collide<LAT, S, T>(f[j], xi, L1, L2, hk ^ (local * 0x27d4eb2du));
-    }
-    if (both) {
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                V v;
-                v.x = f[0][s][k];
-                v.y = f[1][s][k];
-                *reinterpret_cast<V*>(p.fout + (size_t)(s * Q + k) * p.total_nodes + c0) = v;
-            }
-    } else {
-#pragma unroll
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + c0] = f[0][s][k];
-    }
+    if constexpr (MASS) write_mass_partials_pair<S>(xs, active, p.mass);
 }
 
 // Batches take the two-nodes-per-thread shape on the lattices with Q <= 5 (the
@@ -332,9 +352,9 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
             if constexpr (batch_pair_lattice<LAT, S, T>()) {
                 if (a.nodes_per_thread == 2) {
                     if (a.dirichlet)
-                        k_batch_step_pair<LAT, S, T, true><<<blocks, kBlock / 2, 0, a.stream>>>(p, xb);
+                        k_batch_step_pair<LAT, S, T, true, false><<<blocks, kBlock / 2, 0, a.stream>>>(p, xb);
                     else
-                        k_batch_step_pair<LAT, S, T, false><<<blocks, kBlock / 2, 0, a.stream>>>(p, nullptr);
+                        k_batch_step_pair<LAT, S, T, false, false><<<blocks, kBlock / 2, 0, a.stream>>>(p, nullptr);
                     break;
                 }
             }
@@ -344,6 +364,15 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
                 k_batch_step<LAT, S, T, false, false><<<blocks, kBlock, 0, a.stream>>>(p, nullptr);
             break;
         case BOP_STEP_MASS:
+            if constexpr (batch_pair_lattice<LAT, S, T>()) {
+                if (a.nodes_per_thread == 2) {
+                    if (a.dirichlet)
+                        k_batch_step_pair<LAT, S, T, true, true><<<blocks, kBlock / 2, 0, a.stream>>>(p, xb);
+                    else
+                        k_batch_step_pair<LAT, S, T, false, true><<<blocks, kBlock / 2, 0, a.stream>>>(p, nullptr);
+                    break;
+                }
+            }
             if (a.dirichlet)
                 k_batch_step<LAT, S, T, true, true><<<blocks, kBlock, 0, a.stream>>>(p, xb);
             else

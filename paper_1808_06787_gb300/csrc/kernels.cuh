@@ -146,21 +146,62 @@ __device__ __forceinline__ void block_reduce_pair(double& s, double& c, double2*
     __syncthreads();
 }
 
+// Round-to-nearest-even integer of v for |v| <= 2^42, by float additions: adding
+// c = 1.5 * 2^45 rounds v to a multiple of 2^22 whose quotient k is the
+// difference of the sum's bit pattern and c's (the sum stays in c's binade);
+// the remainder r = v - k 2^22 (|r| <= 2^21) is exact and is rounded the same
+// way with 1.5 * 2^23, and since k 2^22 is even, round(v) = k 2^22 + round(r)
+// with the same ties.  (It replaces the 64-bit float-to-integer conversion,
+// which issues at the FP64 rate, a few per clock per SM.)
+__device__ __forceinline__ long long round_to_ll(float v)
+{
+    const float c = 0x1.8p45f, d = 0x1.8p23f;
+    const float sum = __fadd_rn(v, c);
+    const int k = __float_as_int(sum) - __float_as_int(c);
+    const float r = __fadd_rn(v, -__fadd_rn(sum, -c));
+    const int j = __float_as_int(__fadd_rn(r, d)) - __float_as_int(d);
+    return (long long)k * (1ll << 22) + j;
+}
+
+// The block's sums of N fixed-point values per thread, written to out_row[0..N),
+// with one barrier: each warp adds its values by shuffles, lane 0 parks them in
+// shared memory, and thread s < N adds slot s of the warps in warp order.
+// (Integer sums are exact, so the partials do not depend on the grouping.)
+// Called once, at the end of a kernel (the shared slots are not reused).
+template <int N>
+__device__ __forceinline__ void block_fixed_partials(long long (&q)[N], long long* out_row)
+{
+    __shared__ long long red[kBlock / 32][N];
+#pragma unroll
+    for (int s = 0; s < N; ++s)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) q[s] += __shfl_down_sync(0xffffffffu, q[s], off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int s = 0; s < N; ++s) red[warp][s] = q[s];
+    __syncthreads();
+    if (threadIdx.x < N) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+        out_row[threadIdx.x] = t;
+    }
+}
+
 // Per-block partial sums of the n = S + 1 mole fractions (zero for idle threads).
 template <int S>
 __device__ __forceinline__ void write_mass_partials(const float (&xi)[S + 1], bool active,
                                                     const MassOut& m)
 {
-    __shared__ long long red[kBlock / 32];
     const float scale = __int_as_float((127 + m.shift) << 23);  // 2^shift, exact
-    long long* out = static_cast<long long*>(m.partials);
+    long long q[S + 1];
 #pragma unroll
     for (int s = 0; s <= S; ++s) {
         // |xi| beyond 4 (already flagged) is clipped so that sums cannot overflow
         const float v = active ? fminf(fmaxf(xi[s], -4.0f), 4.0f) : 0.0f;
-        const long long q = block_reduce_fixed(__float2ll_rn(v * scale), red);
-        if (threadIdx.x == 0) out[(size_t)blockIdx.x * (S + 1) + s] = q;
+        q[s] = round_to_ll(__fmul_rn(v, scale));
     }
+    block_fixed_partials<S + 1>(q, static_cast<long long*>(m.partials) + (size_t)blockIdx.x * (S + 1));
 }
 
 template <int S>
@@ -276,9 +317,14 @@ __device__ __forceinline__ void load_pair_y(const T* __restrict__ fin, uint32_t 
     }
 }
 
+// Blocks of kBlock / 2 threads per SM asked of the compiler: for each lattice
+// the largest count at which the plain step compiles without spilling (ternary
+// D1Q3 and D2Q4 at 40 registers, D2Q5 at 48, D3Q6 and D3Q7 at 64).  Measured on
+// the full-size grids, each is faster than fewer blocks, and one more step up
+// (which spills) is slower.
 template <int LAT, int S, typename T>
 struct PairOccupancy {
-    static constexpr int value = S <= 1 ? 12 : 8;  // blocks of kBlock / 2 threads per SM
+    static constexpr int value = S <= 1 ? 12 : (Lattice<LAT>::Q <= 4 ? 12 : (Lattice<LAT>::Q == 5 ? 10 : 8));
 };
 
 // Mass partials of a pair kernel's block (the block partition of k_step, so the
@@ -288,18 +334,16 @@ template <int S>
 __device__ __forceinline__ void write_mass_partials_pair(const float (&xi)[2][S + 1], bool active,
                                                          const MassOut& m)
 {
-    __shared__ long long red[kBlock / 32];
     const float scale = __int_as_float((127 + m.shift) << 23);  // 2^shift, exact
-    long long* out = static_cast<long long*>(m.partials);
+    long long q[S + 1];
 #pragma unroll
     for (int s = 0; s <= S; ++s) {
-        long long q = 0;
+        q[s] = 0;
 #pragma unroll
         for (int j = 0; j < 2; ++j)
-            q += __float2ll_rn((active ? fminf(fmaxf(xi[j][s], -4.0f), 4.0f) : 0.0f) * scale);
-        q = block_reduce_fixed(q, red);
-        if (threadIdx.x == 0) out[(size_t)blockIdx.x * (S + 1) + s] = q;
+            q[s] += round_to_ll(__fmul_rn(active ? fminf(fmaxf(xi[j][s], -4.0f), 4.0f) : 0.0f, scale));
     }
+    block_fixed_partials<S + 1>(q, static_cast<long long*>(m.partials) + (size_t)blockIdx.x * (S + 1));
 }
 
 // MASS: the last step of a call, which also tests the mole fractions' range and
