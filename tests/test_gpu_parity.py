@@ -260,6 +260,64 @@ def test_graph_replay_equals_single_steps_and_is_deterministic():
     assert np.array_equal(a.mass(), ma)
 
 
+@pytest.mark.parametrize("lattice,grid,n", [("D2Q9", (40, 30), 4), ("D2Q5", (2048, 1024), 3),
+                                            ("D3Q7", (128, 128, 128), 3)])
+def test_call_graphs_equal_single_steps(lattice, grid, n):
+    """Calls of up to 64 steps replay one graph per (length, buffer parity), the
+    four most recent kept; longer calls take the 32/16/8/4/2-step graphs.  A
+    sequence of calls of mixed lengths (cache hits from both parities, evictions,
+    lengths above 64, single steps) equals the same number of single steps bit
+    for bit, fields and masses, on the one-node and the two-nodes-per-thread
+    kernels (the 2^21-node grids)."""
+    from paper_1808_06787_gb300 import Solver
+
+    D = sy.random_D(n, seed=31)
+    nx, ny = grid[0], grid[1]
+    nz = grid[2] if len(grid) == 3 else 1
+    x0 = sy.sin_modes(n, nx, ny, amp=0.1, seed=32) if nz == 1 else sy.two_bulb(nx, ny, nz, width=4.0)
+    x0 = torch.from_numpy(x0).float().cuda()
+    bc = (W, W, P, P, P, P)
+    calls = [5, 20, 3, 64, 7, 20, 11, 2, 33, 64, 20, 65, 1, 6, 20]
+    a = Solver(lattice, D, grid, bc=bc)
+    a.set_state(x0)
+    for c in calls:
+        a.step(c)
+    b = Solver(lattice, D, grid, bc=bc)
+    b.set_state(x0)
+    for _ in range(sum(calls)):
+        b.step(1)
+    assert a.steps_done == b.steps_done == sum(calls)
+    assert torch.equal(a.moments(), b.moments())
+    assert np.array_equal(a.mass(), b.mass())
+    assert a.status() == b.status() == 0
+
+
+def test_call_graphs_follow_a_new_reference_composition():
+    """The captured graphs hold the kernel arguments: changing the frozen
+    mode's reference composition between two calls of the same length must
+    take effect in the second call."""
+    from paper_1808_06787_gb300 import Solver
+
+    D = sy.random_D(3, seed=33)
+    x0 = torch.from_numpy(sy.sin_modes(3, 48, 40, amp=0.05, seed=34)).double().cuda()
+    ref1 = np.array([0.3, 0.3, 0.4])
+    ref2 = np.array([0.5, 0.2, 0.3])
+
+    def run(single):
+        s = Solver("D2Q5", D, (48, 40), dtype=torch.float64, relax="frozen")
+        s.set_state(x0)
+        for ref in (ref1, ref2):
+            s.set_reference(ref)
+            if single:
+                for _ in range(20):
+                    s.step(1)
+            else:
+                s.step(20)
+        return s.moments()
+
+    assert torch.equal(run(False), run(True))
+
+
 def test_mass_matches_field_sum():
     from paper_1808_06787_gb300 import Solver
 
