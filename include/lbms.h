@@ -22,11 +22,15 @@
  *   J[sigma][a][z][y][x] with a = 0..dim-1.  2D lattices use nz = 1.
  * - Element type of every field is the handle's dtype (float or double).
  * - Buffers may be device memory or host memory; the library asks the CUDA
- *   runtime which one a pointer is.  Host buffers are copied through a bounded
- *   staging area of the workspace; pinned host memory gives full bandwidth.
+ *   runtime which one a pointer is.  Pinned (page-locked) host buffers are read
+ *   or written by the kernels in place, through the device's mapping of pinned
+ *   memory (no staging copies); pageable host buffers are copied through a
+ *   bounded staging area of the workspace.  A host input is read, and a host
+ *   output written, before the call returns.
  * - Everything is ordered on the handle's CUDA stream.  Calls that return data
- *   to host memory (lbms_mass, host outputs of lbms_moments) synchronise that
- *   stream; all other calls are asynchronous.
+ *   to host memory (lbms_mass, host outputs of lbms_moments) or read host
+ *   inputs (lbms_set_state) synchronise that stream; all other calls are
+ *   asynchronous.
  * - The library allocates no device memory.  The caller owns the workspace and
  *   every field buffer.  The handle itself is a small host allocation.
  * - Errors are reported by return code; lbms_last_error() gives a message.
@@ -152,7 +156,7 @@ int lbms_create(lbms_t** out, int lattice, int n_species, const int grid[3], con
  * species, [n][nz][ny][nx] of the handle's dtype, host or device.  Each node
  * must be finite and sum to 1 within 1e-5; otherwise LBMS_FLAG_INIT is raised
  * (read it with lbms_status) and the state is still written.  Resets the step
- * counter to 0.
+ * counter to 0.  A host x0 synchronises the stream (it may be reused on return).
  */
 int lbms_set_state(lbms_t* h, const void* x0);
 
@@ -442,7 +446,8 @@ int lbms_batch_create(lbms_batch_t** out, int lattice, int n_species, int count,
  * Initialise every instance from mole fractions (Sec. 4 initialisation, as
  * lbms_set_state).  Instance i's field is [n][nz][ny][nx] at element offset
  * offsets[i] of x0; offsets == NULL means packed (instance after instance).
- * x0 may be host or device memory; a host x0 synchronises the stream.
+ * x0 may be host or device memory; a host x0 synchronises the stream (it may
+ * be reused on return).
  */
 int lbms_batch_set_state(lbms_batch_t* b, const void* x0, const int64_t* offsets);
 

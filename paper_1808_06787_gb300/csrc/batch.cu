@@ -511,11 +511,14 @@ int lbms_batch_set_state(lbms_batch_t* b, const void* x0, const int64_t* offsets
     const long long* uoff = user_offsets(b, offsets);
     BArgs a = bargs(b, b->stream, 0, b->lay.total_blocks);
     a.fout = b->f[0];
-    if (is_dev(x0)) {
+    const void* alias = pinned_alias(x0);
+    if (alias || is_dev(x0)) {
+        // device memory, or pinned host memory read by the kernel in place
         e = cudaMemcpyAsync(b->foff_dev, uoff, sizeof(long long) * b->count, cudaMemcpyHostToDevice, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "offset upload");
-        a.field_in = x0;
+        a.field_in = alias ? alias : x0;
         e = bdispatch(b, BOP_INIT, a);
+        if (e == cudaSuccess && alias) e = cudaStreamSynchronize(b->stream);  // x0 is free on return
         return e == cudaSuccess ? LBMS_OK : bcuda(b, e, "batch init kernel");
     }
     // host source: pack consecutive instances into the staging area
@@ -609,13 +612,16 @@ int lbms_batch_moments(lbms_batch_t* b, void* x_sigma, void* J_sigma, const int6
     BArgs a = bargs(b, b->stream, 0, b->lay.total_blocks);
     a.fin = b->steps > 0 ? b->f[1 - b->cur] : nullptr;
     a.fout = b->f[b->cur];
-    const bool xdev = is_dev(x_sigma), jdev = J_sigma ? is_dev(J_sigma) : true;
+    // device memory, or pinned host memory written by the kernel in place
+    void* xalias = pinned_alias(x_sigma);
+    void* jalias = J_sigma ? pinned_alias(J_sigma) : nullptr;
+    const bool xdev = xalias || is_dev(x_sigma), jdev = J_sigma ? (jalias || is_dev(J_sigma)) : true;
     cudaError_t e;
     if (xdev && jdev) {
         e = cudaMemcpyAsync(b->foff_dev, uoff, sizeof(long long) * b->count, cudaMemcpyHostToDevice, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "offset upload");
-        a.field_x = x_sigma;
-        a.field_J = J_sigma;
+        a.field_x = xalias ? xalias : x_sigma;
+        a.field_J = jalias ? jalias : J_sigma;
         e = bdispatch(b, BOP_MOMENTS, a);
         if (e != cudaSuccess) return bcuda(b, e, "batch moments kernel");
         e = cudaStreamSynchronize(b->stream);  // the offsets came from pageable memory

@@ -455,6 +455,16 @@ bool is_device_ptr(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+void* pinned_alias(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 cudaError_t device_sm_count(int* sms)
 {
     static std::mutex mu;
@@ -625,10 +635,13 @@ int lbms_set_state(lbms_t* h, const void* x0)
     h->mass_valid = false;
     KArgs a = base_args(h, h->stream);
     a.fout = h->f[0];
-    if (is_device_ptr(x0)) {
-        a.field_in = x0;
+    const void* alias = pinned_alias(x0);
+    if (alias || is_device_ptr(x0)) {
+        // device memory, or pinned host memory read by the kernel in place
+        a.field_in = alias ? alias : x0;
         a.c0 = 0; a.c1 = h->cells; a.stride = h->cells;
         e = dispatch(h, OP_INIT, a);
+        if (e == cudaSuccess && alias) e = cudaStreamSynchronize(h->stream);  // x0 is free on return
         return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "init kernel");
     }
     const uint32_t chunk = (uint32_t)(h->lay.staging_bytes / (h->n * h->es));
@@ -646,7 +659,8 @@ int lbms_set_state(lbms_t* h, const void* x0)
         e = dispatch(h, OP_INIT, a);
         if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
     }
-    return LBMS_OK;
+    e = cudaStreamSynchronize(h->stream);  // x0 is free on return
+    return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "cudaStreamSynchronize");
 }
 
 int lbms_set_boundary(lbms_t* h, int face, const double* xi_b)
@@ -782,15 +796,31 @@ int moments_impl(lbms_t* h, void* x_sigma, void* J_sigma, void* G_sigma)
     a.fout = h->f[h->cur];
     a.halo_recv[0] = h->halo_recv[1 - h->cur][0];
     a.halo_recv[1] = h->halo_recv[1 - h->cur][1];
-    const bool dev = (!x_sigma || is_device_ptr(x_sigma)) && (!J_sigma || is_device_ptr(J_sigma)) &&
-                     (!G_sigma || is_device_ptr(G_sigma));
+    // each output: device memory, pinned host memory written by the kernel in
+    // place, or pageable host memory (through the staging area)
+    void* outs_in[3] = {x_sigma, J_sigma, G_sigma};
+    void* direct[3] = {nullptr, nullptr, nullptr};
+    bool all_direct = true, any_pinned = false;
+    for (int o = 0; o < 3; ++o) {
+        if (!outs_in[o]) continue;
+        void* alias = pinned_alias(outs_in[o]);
+        if (alias) {
+            direct[o] = alias;
+            any_pinned = true;
+        } else if (is_device_ptr(outs_in[o])) {
+            direct[o] = outs_in[o];
+        } else {
+            all_direct = false;
+        }
+    }
     cudaError_t e;
-    if (dev) {
-        a.field_x = x_sigma;
-        a.field_J = J_sigma;
-        a.field_G = G_sigma;
+    if (all_direct) {
+        a.field_x = direct[0];
+        a.field_J = direct[1];
+        a.field_G = direct[2];
         a.c0 = 0; a.c1 = h->cells; a.stride = h->cells;
         e = dispatch(h, OP_MOMENTS, a);
+        if (e == cudaSuccess && any_pinned) e = cudaStreamSynchronize(h->stream);  // host outputs complete
         return e == cudaSuccess ? LBMS_OK : cuda_fail(h, e, "moments kernel");
     }
     // component planes in the staging chunk: x (n), J (n * dim), G (n * dim)

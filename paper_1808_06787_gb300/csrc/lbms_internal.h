@@ -108,6 +108,13 @@ inline uint32_t partial_slots(uint32_t cells)
 // True if the runtime reports p as device (or managed) memory of this process.
 bool is_device_ptr(const void* p);
 
+// The address under which kernels read and write pinned host memory (with
+// unified addressing every pinned allocation is mapped into the device's
+// address space), or null for pageable host memory and for device memory.
+// Kernels then move host fields directly over the host link, without staging
+// copies.
+void* pinned_alias(const void* p);
+
 // Helpers of the host runtime shared with lbms_mass_noalloc (mass_noalloc.cu):
 // fraction bits of the FP32 fixed-point mass partials for a grid, the final
 // reduction of per-block partials into n doubles, and the thread's message for

@@ -635,11 +635,10 @@ class BatchSolver:
 
     def moments(self, flux: bool = False, out_device=None):
         dev = self.device if out_device is None else torch.device(out_device)
-        x = torch.empty(int(self.offsets[-1]), dtype=self.dtype, device=dev)
-        J = torch.empty(int(self.offsets[-1]) * self.dim, dtype=self.dtype, device=dev) if flux else None
-        if dev.type == "cpu":
-            x = x.pin_memory()
-            J = J.pin_memory() if J is not None else None
+        pin = dev.type == "cpu"  # host outputs pinned: the moments kernel writes them in place
+        x = torch.empty(int(self.offsets[-1]), dtype=self.dtype, device=dev, pin_memory=pin)
+        J = (torch.empty(int(self.offsets[-1]) * self.dim, dtype=self.dtype, device=dev, pin_memory=pin)
+             if flux else None)
         _bcheck(self._h, load().lbms_batch_moments(self._h, ctypes.c_void_p(x.data_ptr()),
                                                    ctypes.c_void_p(J.data_ptr()) if J is not None else None,
                                                    None), "lbms_batch_moments")

@@ -141,8 +141,15 @@ def test_batch_host_buffers_and_offsets():
     b = BatchSolver("D2Q9", Ds, grids, bcs=bcs, dtype=torch.float64)
     b.set_state(flat.clone())  # pageable host source, packed through the staging area
     b.step(9)
-    xb, Jb = b.moments(flux=True, out_device="cpu")
+    xb, Jb = b.moments(flux=True, out_device="cpu")  # pinned outputs, written in place
     assert torch.equal(xa.cpu(), xb) and torch.equal(Ja.cpu(), Jb)
+    c = BatchSolver("D2Q9", Ds, grids, bcs=bcs, dtype=torch.float64)
+    fp = flat.clone().pin_memory()
+    c.set_state(fp)  # pinned host source, read by the init kernel in place
+    fp.fill_(0.0)
+    c.step(9)
+    xc, Jc = c.moments(flux=True)
+    assert torch.equal(xa, xc) and torch.equal(Ja, Jc)
 
 
 def test_tuner_picks_a_valid_schedule():

@@ -215,9 +215,10 @@ def test_d2q9_fp32_2048sq_n5_full_size():
 
 
 def test_host_buffers_match_device_buffers():
-    """Host (pageable and pinned) inputs/outputs go through the chunked staging
-    path; results equal the device path bit for bit.  The fields here exceed the
-    16 MiB staging area, so several chunks are used."""
+    """Pageable host inputs/outputs go through the chunked staging path (the
+    fields here exceed the 16 MiB staging area, so several chunks are used);
+    pinned host buffers are read and written by the kernels in place; results
+    equal the device path bit for bit."""
     from paper_1808_06787_gb300 import Solver
 
     D = sy.random_D(3, seed=9)
@@ -239,6 +240,17 @@ def test_host_buffers_match_device_buffers():
     c.step(7)
     xc = c.moments()
     assert torch.equal(xa, xc)
+    xp = torch.empty(c.field_shape, dtype=torch.float64).pin_memory()
+    Jp = torch.empty(c.flux_shape, dtype=torch.float64).pin_memory()
+    c.moments(xp, Jp)  # both outputs pinned: written by the moments kernel in place
+    assert torch.equal(xa.cpu(), xp) and torch.equal(Ja.cpu(), Jp)
+    # a pinned input may be overwritten as soon as set_state returns
+    x0p = x0t.clone().pin_memory()
+    d = Solver("D2Q5", D, (1024, 1000), dtype=torch.float64)
+    d.set_state(x0p)
+    x0p.fill_(0.0)
+    d.step(7)
+    assert torch.equal(xa, d.moments())
 
 
 def test_graph_replay_equals_single_steps_and_is_deterministic():
