@@ -273,7 +273,7 @@ def test_graph_replay_equals_single_steps_and_is_deterministic():
 
 
 @pytest.mark.parametrize("lattice,grid,n", [("D2Q9", (40, 30), 4), ("D2Q5", (2048, 1024), 3),
-                                            ("D3Q7", (128, 128, 128), 3)])
+                                            ("D3Q7", (128, 128, 128), 3), ("D2Q9", (512, 384), 5)])
 def test_call_graphs_equal_single_steps(lattice, grid, n):
     """Calls of up to 64 steps replay one graph per (length, buffer parity), the
     four most recent kept; longer calls take the 32/16/8/4/2-step graphs.  A
