@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p, const T
 #pragma unroll
             for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + cell] = f[s][k];
     }
-    if (MASS) write_mass_partials<S>(xi, active, p.mass);
+    if (MASS) write_mass_partials<S>(xi, active, p.mass, blockIdx.x);
 }
 
 // Two nodes per thread, as k_step_pair: blocks of kBlock / 2 threads cover one
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kBlock / 2, 12)
                 for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + c0] = f[0][s][k];
         }
     }
-    if constexpr (MASS) write_mass_partials_pair<S>(xs, active, p.mass);
+    if constexpr (MASS) write_mass_partials_pair<S>(xs, active, p.mass, blockIdx.x);
 }
 
 // Batches take the two-nodes-per-thread shape on the lattices with Q <= 5 (the
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_mass(BatchParams<T> p)
             for (int k = 0; k < Q; ++k) f[s][k] = p.fout[(size_t)(s * Q + k) * p.total_nodes + cell];
         mole_fractions<LAT, S, T>(f, xi);
     }
-    write_mass_partials<S>(xi, active, p.mass);
+    write_mass_partials<S>(xi, active, p.mass, blockIdx.x);
 }
 
 // f+ = w_k xi at t = 0 for each instance, from its [n][cells] block of x_in.

@@ -338,6 +338,9 @@ cudaError_t launch_step(const lbms_t* h, int src, bool mass, cudaStream_t st)
     a.partials = h->partials;
     a.clock_in = h->clock + src;
     a.clock_out = h->clock + (1 - src);
+    // steps alternate their direction through the grid: each starts where the
+    // one before ended, whose last writes are still in L2
+    a.reverse = src;
     return dispatch(h, mass ? OP_STEP_MASS : OP_STEP, a);
 }
 

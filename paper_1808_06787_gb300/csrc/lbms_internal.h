@@ -50,6 +50,7 @@ struct KArgs {
     uint32_t* status = nullptr;
     const uint32_t* clock_in = nullptr;  // step counter read by a step
     uint32_t* clock_out = nullptr;       // step counter written by a step
+    int reverse = 0;                     // step: blocks take the grid from its end
     cudaStream_t stream = nullptr;
 };
 
