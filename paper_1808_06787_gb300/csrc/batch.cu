@@ -239,6 +239,7 @@ cudaError_t bstep(const lbms_batch_t* b, int src, bool mass, uint32_t b0, uint32
     a.fin = b->f[src];
     a.fout = b->f[1 - src];
     a.parity = src;
+    a.reverse = src;  // alternate steps take the blocks from the end (same-box A/B: +0.35 %)
     a.nodes_per_thread = b->shape + 1;
     return bdispatch(b, mass ? BOP_STEP_MASS : BOP_STEP, a);
 }

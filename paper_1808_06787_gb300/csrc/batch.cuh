@@ -37,6 +37,7 @@ struct BArgs {
     int relax = LBMS_RELAX_MAGIC;
     uint32_t* clock = nullptr;                // [count][2] step counters
     int parity = 0;                           // counter word read (= index of fin)
+    int reverse = 0;                          // steps: blocks taken from the end of the range
     void* partials = nullptr;                 // [total_blocks][n]
     int fixed_shift = 32;
     uint32_t* status = nullptr;
@@ -69,6 +70,7 @@ struct BatchParams {
     int relax;
     uint32_t* clock;
     int parity;
+    int reverse;  // steps: blocks taken from the end of the launch's range (grid_block)
     MassOut mass;  // partials pointer already offset to block_begin
     uint32_t* status;
     const T* x_in;
@@ -87,7 +89,8 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p, const T
 {
     using L = Lattice<LAT>;
     constexpr int Q = L::Q;
-    const uint32_t blk = p.block_begin + blockIdx.x;
+    const uint32_t lb = grid_block(p.reverse);  // alternate steps take the blocks from the end
+    const uint32_t blk = p.block_begin + lb;
     const uint32_t id = p.blk_inst[blk];
     const BatchInst d = p.inst[id];
     const uint32_t local = (blk - d.block0) * kBlock + threadIdx.x;
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchParams<T> p, const T
 #pragma unroll
             for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + cell] = f[s][k];
     }
-    if (MASS) write_mass_partials<S>(xi, active, p.mass, blockIdx.x);
+    if (MASS) write_mass_partials<S>(xi, active, p.mass, lb);
 }
 
 // Two nodes per thread, as k_step_pair: blocks of kBlock / 2 threads cover one
@@ -135,7 +138,8 @@ __global__ void __launch_bounds__(kBlock / 2, 12)
     using V = typename Pair<T>::type;
     constexpr int Q = L::Q;
     constexpr bool REST = L::K0 == 1;  // lattices without a rest velocity gather every population
-    const uint32_t blk = p.block_begin + blockIdx.x;
+    const uint32_t lb = grid_block(p.reverse);
+    const uint32_t blk = p.block_begin + lb;
     const uint32_t id = p.blk_inst[blk];
     const BatchInst d = p.inst[id];
     const uint32_t local0 = (blk - d.block0) * kBlock + 2 * threadIdx.x;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(kBlock / 2, 12)
                 for (int k = 0; k < Q; ++k) p.fout[(size_t)(s * Q + k) * p.total_nodes + c0] = f[0][s][k];
         }
     }
-    if constexpr (MASS) write_mass_partials_pair<S>(xs, active, p.mass, blockIdx.x);
+    if constexpr (MASS) write_mass_partials_pair<S>(xs, active, p.mass, lb);
 }
 
 // Batches take the two-nodes-per-thread shape on the lattices with Q <= 5 (the
@@ -335,6 +339,7 @@ cudaError_t batch_launch(BatchOp op, const BArgs& a)
     p.relax = a.relax;
     p.clock = a.clock;
     p.parity = a.parity;
+    p.reverse = a.reverse;
     const size_t rec = sizeof(T) == 8 ? sizeof(double2) : sizeof(long long);
     p.mass.partials = a.partials ? static_cast<char*>(a.partials) + (size_t)a.block_begin * (S + 1) * rec
                                  : nullptr;
