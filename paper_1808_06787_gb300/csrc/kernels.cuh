@@ -222,10 +222,12 @@ __device__ __forceinline__ void write_mass_partials(const double (&xi)[S + 1], b
 // The block of the grid a step kernel's block takes.  Steps alternate: a
 // forward step takes the grid in order; a reverse step takes chunks of
 // kRevChunk blocks from the grid's end, each chunk in order, so that it starts
-// on the chunk the forward step wrote last, which is still in L2, while its
+// on the blocks the forward step wrote last, which are still in L2, while its
 // accesses still ascend within a chunk.  (A permutation of the blocks: the
-// last chunk taken is the remainder at the grid's start.)
-constexpr uint32_t kRevChunk = 1024;
+// last chunk taken is the remainder at the grid's start.)  Chunks of 32 to
+// 256 blocks measured alike and best; 1024 slightly and 4096 or the whole
+// grid clearly slower (D3Q7 256^3: 1.045, 1.043, 1.035, 1.033).
+constexpr uint32_t kRevChunk = 64;
 
 __device__ __forceinline__ uint32_t grid_block(int reverse)
 {
