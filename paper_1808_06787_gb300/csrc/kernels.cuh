@@ -337,15 +337,16 @@ __device__ __forceinline__ void load_pair_y(const T* __restrict__ fin, uint32_t 
     }
 }
 
-// Blocks of kBlock / 2 threads per SM asked of the compiler: for each lattice
-// the largest count at which the plain step compiles without spilling (ternary
-// D1Q3 and D2Q4 at 40 registers, D2Q5 at 48, D3Q6 at 56, D3Q7 at 64).  Measured
-// on the full-size grids, each is faster than fewer blocks, and one more step up
-// (which spills) is slower.
+// Blocks of kBlock / 2 threads per SM asked of the compiler, measured on the
+// full-size grids: for D1Q3, D2Q4, D2Q5 and D3Q6 (ternary) the largest count at
+// which the plain step compiles without spilling (40, 40, 48 and 56
+// registers), each faster than fewer blocks while one more (spilling) is
+// slower; for D3Q7, 9 blocks at 56 registers with a 24-byte spill (0.3 %
+// faster than 8 blocks without; 10 blocks, 48 registers: 2 % slower).
 template <int LAT, int S, typename T>
 struct PairOccupancy {
     static constexpr int Q = Lattice<LAT>::Q;
-    static constexpr int value = S <= 1 ? 12 : (Q <= 4 ? 12 : (Q == 5 ? 10 : (Q == 6 ? 9 : 8)));
+    static constexpr int value = S <= 1 ? 12 : (Q <= 4 ? 12 : (Q == 5 ? 10 : 9));
 };
 
 // Mass partials of a pair kernel's block (the block partition of k_step, so the
