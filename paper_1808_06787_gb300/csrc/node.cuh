@@ -85,14 +85,40 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
         }
     }
     if constexpr (S == 2) {
-        // ternary mixtures (Remark IV): Lambda_1/2 = adj(K) (B/2) / det(K), one
-        // reciprocal; det(K) > 0 because B's eigenvalues are real and non-negative
-        const T rdet = recip(K[0][0] * K[1][1] - K[0][1] * K[1][0]);
+        // ternary mixtures (Remark IV): Lambda_1/2 = adj(K) (B/2) / det(K) = N / d;
+        // d = det(K) > 0 because B's eigenvalues are real and non-negative.  With
+        // h = N_ii / d, Eq. 3-16 for l = 2h reads lambda_2/2 = 4 (N_ii - d) /
+        // (N_ii - 4 d), so one reciprocal of d (N_00 - 4d) (N_11 - 4d) gives 1/d
+        // and both diagonal entries of Lambda_2/2 (N_ii - 4d < 0 for l < 8).
+        const T d = K[0][0] * K[1][1] - K[0][1] * K[1][0];
         const T b00 = L1[0][0], b01 = L1[0][1], b10 = L1[1][0], b11 = L1[1][1];
-        L1[0][0] = (K[1][1] * b00 - K[0][1] * b10) * rdet;
-        L1[0][1] = (K[1][1] * b01 - K[0][1] * b11) * rdet;
-        L1[1][0] = (K[0][0] * b10 - K[1][0] * b00) * rdet;
-        L1[1][1] = (K[0][0] * b11 - K[1][0] * b01) * rdet;
+        const T n00 = K[1][1] * b00 - K[0][1] * b10;
+        const T n01 = K[1][1] * b01 - K[0][1] * b11;
+        const T n10 = K[0][0] * b10 - K[1][0] * b00;
+        const T n11 = K[0][0] * b11 - K[1][0] * b01;
+        T rdet;
+        if (relax != LBMS_RELAX_SRT) {  // Eq. 3-16 (the frozen mode uses it too)
+            const T p0 = n00 - T(4) * d, p1 = n11 - T(4) * d;
+            const T pp = p0 * p1;
+            const T inv = recip(d * pp);
+            rdet = inv * pp;
+            const T q = inv * d;
+            L2[0][0] = T(4) * (n00 - d) * (q * p1);
+            L2[1][1] = T(4) * (n11 - d) * (q * p0);
+        } else {
+            rdet = recip(d);
+        }
+        L1[0][0] = n00 * rdet;
+        L1[0][1] = n01 * rdet;
+        L1[1][0] = n10 * rdet;
+        L1[1][1] = n11 * rdet;
+        L2[0][1] = L1[0][1];
+        L2[1][0] = L1[1][0];
+        if (relax == LBMS_RELAX_SRT) {
+            L2[0][0] = L1[0][0];
+            L2[1][1] = L1[1][1];
+        }
+        return;
     } else {
 #pragma unroll
         for (int p = 0; p < S; ++p) {
@@ -120,18 +146,10 @@ __device__ __forceinline__ void relaxation_matrices(const T (&xi)[S + 1], const 
         for (int j = 0; j < S; ++j) L2[i][j] = L1[i][j];
     if (relax != LBMS_RELAX_SRT) {  // Eq. 3-16 (the frozen mode uses it too)
         // Eq. 3-16 with l = 2 h: lambda_2/2 = 4 (h - 1) / (h - 4)
-        if constexpr (S == 2) {
-            // both diagonal entries with one reciprocal
-            const T a = L1[0][0] - T(4), b = L1[1][1] - T(4);
-            const T r = recip(a * b);
-            L2[0][0] = T(4) * (L1[0][0] - T(1)) * (b * r);
-            L2[1][1] = T(4) * (L1[1][1] - T(1)) * (a * r);
-        } else {
 #pragma unroll
-            for (int i = 0; i < S; ++i) {
-                const T h = L1[i][i];
-                L2[i][i] = T(4) * (h - T(1)) * recip(h - T(4));  // Eq. 3-16, i == j
-            }
+        for (int i = 0; i < S; ++i) {
+            const T h = L1[i][i];
+            L2[i][i] = T(4) * (h - T(1)) * recip(h - T(4));  // Eq. 3-16, i == j
         }
     }
 }
