@@ -247,10 +247,9 @@ class ClockSampler:
 
 
 # FP64 work of the D2Q5 ternary step per node, counted by ncu on the kernel
-# (DADD + DMUL + 2 DFMA: 61 + 18 + 2 x 39 per node, with the pair form's halves
-# folded into the relaxation matrices).  GB300 issues 2 DFMA per SM and cycle
-# (ncu's peak_sustained of 304 per cycle over its 152 SMs).
-D2Q5_TERNARY_FP64_FLOPS_PER_NODE = 157.0
+# (DADD + DMUL + 2 DFMA: 59 + 21 + 2 x 36 per node).  GB300 issues 2 DFMA per SM
+# and cycle (ncu's peak_sustained of 304 per cycle over its 152 SMs).
+D2Q5_TERNARY_FP64_FLOPS_PER_NODE = 152.0
 DFMA_PER_SM_CLK = 2
 
 
@@ -261,7 +260,7 @@ def fp64_peak_tflops(sms: int, sm_mhz: float) -> float:
 
 def fp64_roofline(wl: "Workload", step_ms: float, sms: int, sm_mhz: float) -> dict:
     """ALU roofline of the L2-resident FP64 workload: its step kernel is bound by the
-    FP64 pipes (55 % of their issue slots busy under ncu), not by HBM.  The peak
+    FP64 pipes (57 % of their issue slots busy under ncu), not by HBM.  The peak
     uses the device's SM count and the SM clock sampled while it ran."""
     flops = D2Q5_TERNARY_FP64_FLOPS_PER_NODE * wl.cells
     achieved = flops / (step_ms * 1e-3) / 1e12
