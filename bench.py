@@ -282,16 +282,20 @@ def fp64_roofline(wl: "Workload", step_ms: float, sms: int, sm_mhz: float) -> di
 def dist_context(backend: str = "nccl"):
     """(world, rank, local_rank, dist-or-None) from the torchrun environment.
 
-    Every rank runs one independent replica of the workload (the solves share
-    no data), so the only collectives are the barriers around the timed region
-    and the maximum of the per-rank times."""
+    The rank's GPU is selected before the process group exists, so that NCCL's
+    communicators bind to it.  Single-solve workloads shard one grid over the
+    ranks (halo exchange every step, masses by one all-reduce); batches and the
+    adjoint run one independent problem per rank."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
     if world > 1:
+        import torch
         import torch.distributed as dist
 
+        if backend == "nccl" and torch.cuda.is_available():
+            torch.cuda.set_device(local)
         if not dist.is_initialized():
             dist.init_process_group(backend)
     return world, rank, local, dist
