@@ -926,7 +926,17 @@ def run_batch(args):
 
 
 def run_adjoint(args):
-    """Adjoint workload as the headline line (see measure_adjoint)."""
+    """Adjoint workload as the headline line (see measure_adjoint).  The gradient
+    of one problem runs on one GPU: under torchrun rank 0 measures it and the
+    other ranks exit without work."""
+    import torch
+
+    world, rank, local, dist = dist_context()
+    if world > 1:
+        torch.cuda.set_device(local)
+        if rank != 0:
+            dist.destroy_process_group()
+            return
     steps = args.steps or ADJOINT_STEPS
     n = 512 if args.grid == 256 else args.grid
     m = measure_adjoint(args.warmup, 0, n=n, steps=steps, e2e=not args.no_e2e)
@@ -950,6 +960,8 @@ def run_adjoint(args):
         "clocks": m["clocks"],
     }
     print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def _oracle_sample_run(wl: Workload, cells_target: int, steps: int):
