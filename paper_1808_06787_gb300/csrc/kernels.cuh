@@ -291,13 +291,14 @@ __global__ void __launch_bounds__(kBlock, StepOccupancy<LAT, S, T>::value) k_ste
 
 // Two nodes per thread (c, c + 1 with c even), for the lattices with Q <= 7 and
 // S <= 2 in FP32, whose per-node instruction count rather than HBM bandwidth
-// limits the one-node kernel: the pair's rest populations (if the lattice has a rest velocity) come
-// in one 8-byte load and every post-collision plane goes out in one 8-byte
-// store, and the per-thread
-// set-up is shared; the per-node arithmetic is that of k_step, so the results
-// are the same bit for bit.  Blocks of kBlock / 2 threads cover kBlock nodes, the
-// partition of k_step.  Needs an even node count (so that every population plane
-// starts at an even node); no cut faces.
+// limits the one-node kernel: the pair's rest populations (if the lattice has a
+// rest velocity) come in one 8-byte load, with an even nx so do the populations
+// that do not move along x (load_pair_y), every post-collision plane goes out in
+// one 8-byte store, and the per-thread set-up is shared; the per-node
+// arithmetic is that of k_step, so the results are the same bit for bit.
+// Blocks of kBlock / 2 threads cover kBlock nodes, the partition of k_step (and
+// the same alternation of directions, grid_block).  Needs an even node count (so
+// that every population plane starts at an even node); no cut faces.
 template <typename T>
 struct Pair;
 template <>
